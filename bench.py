@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Benchmark of the domain decomposition primal-dual TV solver on one GB300.
+
+Workload: ROF denoising of a 4096 x 4096 float32 image (seeded piecewise-constant
+scene of 400 rectangles/disks + Gaussian noise sigma = 0.1), alpha = 8, 32 x 32
+subdomains of 128 x 128, 10 inner iterations per outer iteration, the paper's
+steps (tau = 50, sigma tau = 1/2, tau0 = 10, sigma0 tau0 = 1/8, gamma = 1/(8 tau)).
+
+One step = one outer iteration of Algorithm 1 (interface multiplier update, proximal
+centre, all local solves, assembly), plus every 5th step the energy reduction of the
+outer stopping rule.  Metric: Mpixel-iter/s = H * W * inner iterations / s / 1e6.
+The state (u, torn p, f: ~470 MB) is larger than L2, so no flush is needed.
+
+Also reported: time to relative energy error 1e-4 against a certified J* (fused vs
+plain vs full-dimension GPU paths), the end-to-end number through dd_tv_solve with
+host buffers, the fused kernel's roofline, and the FP64 oracle on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H = W = 4096
+NR = NC = 32
+INNER = 10
+ALPHA = 8.0
+N_SHAPES = 400
+NOISE = 0.1
+SEED = 0
+ENERGY_EVERY = 5
+METRIC = "Mpixel*iter/s at 4096^2 ROF"
+UNIT = "Mpixel*iter/s"
+WORKLOAD = "rof4096: ROF L2 denoising 4096x4096 fp32, alpha=8, 32x32 subdomains of 128x128, 10 inner/outer"
+SMEM_BYTES_PER_PX_ITER = 28  # minimum neighbour exchange per pixel per inner iteration
+JSTAR_FILE = os.path.join(ROOT, "tests", "golden", "jstar_rof4096_seed0.json")
+PROFILE_FILE = os.path.join(ROOT, "profiles", "fused_local_rof4096.md")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-tta", action="store_true", help="skip the time-to-accuracy runs")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.rows = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        self.t0 = time.time()
+
+    def stop(self):
+        if not self.proc:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower() == "active"})
+        loaded = [s for s in sm if s >= 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def make_input():
+    import synth
+    f, clean = synth.rof_image(H, W, N_SHAPES, NOISE, SEED)
+    return f, clean
+
+
+def load_jstar(f):
+    import synth
+    if not os.path.exists(JSTAR_FILE):
+        return None, "no certified J* file"
+    rec = json.load(open(JSTAR_FILE))
+    if rec.get("f_sha256") != synth.array_digest(f):
+        return None, "generated image differs from the one J* was certified on"
+    return rec, None
+
+
+def profile_traffic():
+    """(dram bytes per launch, sha) of the fused kernel from the committed ncu summary,
+    or None when the kernel source changed since the capture."""
+    if not os.path.exists(PROFILE_FILE):
+        return None
+    vals = {}
+    for line in open(PROFILE_FILE):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    src = os.path.join(ROOT, "paper_1901_00682_gb300", "csrc", "kernels_fused.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if vals.get("kernel_source_sha256") != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(f, outer=2):
+    """The FP64 oracle (as it stands) on a bounded sample: `outer` outer iterations of
+    the same 4096^2 workload on the host cores."""
+    import numpy as np
+
+    import oracle
+    pr = oracle.Problem(H, W, NR, NC, fidelity="l2", alpha=ALPHA, inner=INNER)
+    f64 = f.astype(np.float64)
+    st = oracle.dd_init(pr, f64)
+    oracle.dd_run(pr, f64, 0, state=st)  # builds/loads the oracle library
+    t = time.perf_counter()
+    oracle.dd_run(pr, f64, outer, state=st)
+    dt = time.perf_counter() - t
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": H * W * INNER * outer / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{outer} outer iterations (x{INNER} inner) of the 4096^2 32x32-subdomain workload, "
+                      f"FP64, OpenMP over subdomains, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, each step one outer iteration
+    on a bounded sample (the top-left S x S block, subdomains of 128 x 128, 10 inner
+    iterations; S shrinks with the step count)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    f, _ = make_input()
+    # sample size per step keeps the whole run within about a minute of host time
+    S = 512 if args.steps <= 200 else (256 if args.steps <= 2000 else 128)
+    sub = np.ascontiguousarray(f[:S, :S]).astype(np.float64)
+    pr = oracle.Problem(S, S, S // 128, S // 128, fidelity="l2", alpha=ALPHA, inner=INNER)
+    st = oracle.dd_init(pr, sub)
+    oracle.dd_run(pr, sub, args.warmup, state=st)
+    t = time.perf_counter()
+    oracle.dd_run(pr, sub, args.steps, state=st)
+    dt = time.perf_counter() - t
+    val = S * S * INNER * args.steps / dt / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"each step: 1 outer iteration (x{INNER} inner) on the top-left {S}x{S} block of the workload, "
+              f"{S // 128}x{S // 128} subdomains of 128x128, FP64 oracle")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    from paper_1901_00682_gb300 import _lib as L
+
+    L.load()
+    f, _ = make_input()
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    fd = torch.from_numpy(f).to(dev)
+
+    # ---- throughput: resident inputs, K steps
+    p = L.make_params(H, W, NR, NC, fidelity="l2", alpha=ALPHA, inner_iters=INNER, path="fused")
+    s = L.Solver(p, stream)
+    s.load(fd)
+    for q in range(args.warmup):
+        s.iterate(1)
+        if (q + 1) % ENERGY_EVERY == 0:
+            s.current_energy()
+    torch.cuda.synchronize(dev)
+    s.profile_read()
+    s.set_profiling(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for q in range(args.steps):
+        s.iterate(1)
+        if (q + 1) % ENERGY_EVERY == 0:
+            s.current_energy()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    prof_ms, prof_n = s.profile_read()
+    s.set_profiling(False)
+    t_max = ms_total
+    if pg:
+        tt = torch.tensor([ms_total], device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        t_max = float(tt.item())
+    work = H * W * INNER * args.steps
+    value = world * work / (t_max * 1e-3) / 1e6
+
+    # ---- roofline of the fused local solver (dominant kernel)
+    local_avg_ms = prof_ms["local"] / max(prof_n["local"], 1)
+    smem_peak = L.measure_smem_bandwidth()
+    bytes_per_launch = SMEM_BYTES_PER_PX_ITER * H * W * INNER
+    achieved = bytes_per_launch / (local_avg_ms * 1e-3) / 1e9
+    traffic = profile_traffic()
+    iface_avg_ms = prof_ms["interface"] / max(prof_n["interface"], 1)
+    energy_avg_ms = prof_ms["energy"] / max(prof_n["energy"], 1)
+    n_if = 2 * (NR - 1) * W
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    roofline = {
+        "bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s", "frac": achieved / smem_peak,
+        "traffic": traffic,
+        "kernel": "fused local solver (k_fused, cluster of 8 CTAs per 128x128 subdomain)",
+        "peak_source": "measured live: ld.shared probe kernel (dd_tv_measure_smem_bandwidth)",
+        "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": local_avg_ms,
+        "hbm_state_stream": {"bytes_per_launch": 28 * H * W,
+                             "achieved_gbs": 28 * H * W / (local_avg_ms * 1e-3) / 1e9,
+                             "peak_gbs": hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+        "interface_kernel": {"avg_launch_ms": iface_avg_ms, "bytes_per_launch": 24 * n_if,
+                             "achieved_gbs": 24 * n_if / (iface_avg_ms * 1e-3) / 1e9 if iface_avg_ms else None,
+                             "peak_gbs": hbm_peak},
+        "energy_kernel": {"avg_launch_ms": energy_avg_ms, "bytes_per_launch": 8 * H * W,
+                          "achieved_gbs": 8 * H * W / (energy_avg_ms * 1e-3) / 1e9 if energy_avg_ms else None,
+                          "peak_gbs": hbm_peak},
+    }
+
+    # ---- end to end through dd_tv_solve with pinned host buffers
+    f_pin = torch.from_numpy(f).pin_memory()
+    u_pin = torch.empty_like(f_pin).pin_memory()
+    pe = L.make_params(H, W, NR, NC, fidelity="l2", alpha=ALPHA, inner_iters=INNER, path="fused",
+                       outer_iters=args.steps)
+    se = L.Solver(pe, stream)
+    se.solve_host(f_pin.numpy(), None, u_pin.numpy())  # warm-up (graph capture)
+    if pg:
+        pg.barrier()
+    t = time.perf_counter()
+    _, st_e2e, _ = se.solve_host(f_pin.numpy(), None, u_pin.numpy())
+    dt_e2e = time.perf_counter() - t
+    if pg:
+        tt = torch.tensor([dt_e2e], device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        dt_e2e = float(tt.item())
+    e2e = {"value": world * work / dt_e2e / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": 4 * H * W / args.steps, "d2h_bytes_per_step": 4 * H * W / args.steps,
+           "call": "dd_tv_solve(host f, host u), one call of K outer iterations"}
+    se.close()
+
+    # ---- time to relative energy error 1e-4 (fused vs plain vs full-dimension)
+    tta = None
+    if not args.no_tta:
+        rec, why = load_jstar(f)
+        if rec is None:
+            tta = {"skipped": why}
+        else:
+            tta = {"J_star": rec["J_star"], "J_star_rel_gap": rec["rel_gap"], "tol": 1e-4,
+                   "energy_every": ENERGY_EVERY}
+            for path, cap in (("fused", 3000), ("plain", 3000), ("fulldim", 2000)):
+                pt = L.make_params(H, W, NR, NC, fidelity="l2", alpha=ALPHA, inner_iters=INNER, path=path,
+                                   outer_iters=cap, outer_tol=1e-4, energy_ref=rec["J_star"],
+                                   energy_every=ENERGY_EVERY)
+                sp = L.Solver(pt, stream)
+                u_out = torch.empty_like(fd)
+                sp.solve_device(fd, None, u_out)  # warm-up run (graph capture, clocks)
+                torch.cuda.synchronize(dev)
+                t = time.perf_counter()
+                _, stt, rc = sp.solve_device(fd, None, u_out)
+                torch.cuda.synchronize(dev)
+                dt = time.perf_counter() - t
+                tta[path] = {"ms": dt * 1e3, "device_ms": stt.ms, "outer_iters": stt.outer_done,
+                             "rel_err": stt.rel_err, "reached": bool(stt.converged)}
+                sp.close()
+            if tta["fused"]["reached"] and tta["plain"]["reached"]:
+                tta["speedup_vs_plain"] = tta["plain"]["ms"] / tta["fused"]["ms"]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(f)
+
+    if rank == 0:
+        launches = int(sum(prof_n.values()))
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "state (~470 MB) larger than L2; no flush",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "step": "1 outer iteration (interface + fused local solves), energy every 5 steps"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "time_to_accuracy": tta,
+            "clocks": clocks.summary(), "gpu_launches": launches,
+            "launches_by_phase": prof_n, "phase_ms": prof_ms,
+        }
+        print(json.dumps(out), flush=True)
+    s.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * dd_tv.h - C ABI of the GB300 (sm_103a) solver for the primal-dual domain
+ * decomposition method for dual total variation minimisation of Lee & Park,
+ * "A finite element nonoverlapping domain decomposition method with Lagrange
+ * multipliers for the dual total variation minimizations" (Algorithm 1).
+ *
+ * Problem (Section 3, eq. model):  min_u  J(u) = alpha F(u) + TV(u)  on an H x W
+ * image of unit square pixels, TV the anisotropic discrete total variation (the
+ * proposition on the FE/FD equivalence), with one of the fidelities of Section 3:
+ *   DD_TV_L2  : F = 1/2 sum_{T not in D} (u - f)^2     ROF denoising / L2 inpainting
+ *   DD_TV_L1  : F =     sum_{T not in D} |u - f|       TV-L1 denoising / L1 inpainting
+ *   DD_TV_SEG : F = <u, g> + chi_{[0,1]}(u),  g = (f - c1)^2 - (f - c2)^2
+ *                                                      convex Chan-Vese segmentation
+ * D is the optional inpainting domain (mask byte 1 = pixel in D, f ignored there).
+ *
+ * Method (Algorithm 1): the image is split into sub_rows x sub_cols rectangles
+ * (Section 2.4); tile row a covers pixel rows [floor(a H / sub_rows),
+ * floor((a+1) H / sub_rows)), tile columns likewise.  Each outer iteration
+ *   lambda <- lambda + sigma B (2 p~^n - p~^{n-1})         (interface multipliers)
+ *   phat   <- p~^n - tau B^* lambda                         (proximal centre)
+ *   every tile, in parallel: inner_iters accelerated primal-dual iterations on its
+ *   local saddle problem (Section 5, eq. local), warm-started from (u^n, p~^n).
+ * p~ is the torn lowest-order Raviart-Thomas dual field: one normal component per
+ * pixel edge, every tile keeping its own copy on its sides (Section 2.4).
+ *
+ * Conventions for every entry point:
+ *   - images are row-major float32 H x W (u, f) or uint8 H x W (mask);
+ *   - "_host" pointers are ordinary host memory, "_dev" pointers device memory of
+ *     the current CUDA device; the library never keeps a caller's pointer after
+ *     the call returns, and the caller keeps ownership of everything it passes;
+ *   - calls return a dd_tv_status; on failure dd_tv_last_error(h) describes it;
+ *     no call aborts the process or traps the GPU;
+ *   - work is issued on the handle's stream (dd_tv_set_stream); calls that return
+ *     a host value or write host memory synchronise that stream first.
+ * The handle owns all device memory it uses; it is not thread-safe.
+ */
+#ifndef DD_TV_H
+#define DD_TV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dd_tv dd_tv;
+
+typedef enum { DD_TV_L2 = 0, DD_TV_L1 = 1, DD_TV_SEG = 2 } dd_tv_fidelity;
+
+typedef enum {
+  DD_TV_OK = 0,
+  DD_TV_EINVAL = 1,      /* invalid argument (message in dd_tv_last_error)            */
+  DD_TV_ENOMEM = 2,      /* device or host allocation failed                           */
+  DD_TV_ECUDA = 3,       /* a CUDA call failed                                         */
+  DD_TV_ETIMEOUT = 4,    /* a bounded device-side wait ran out                          */
+  DD_TV_ENOTCONV = 5,    /* outer_tol given and not reached within outer_iters          */
+  DD_TV_EUNSUPPORTED = 6 /* valid problem outside what the chosen path implements       */
+} dd_tv_status;
+
+/* Which implementation runs an outer iteration. */
+typedef enum {
+  DD_TV_PATH_FUSED = 0,  /* interface kernel + fused subdomain-per-cluster local solver */
+  DD_TV_PATH_PLAIN = 1,  /* one global-memory kernel per step (comparator)              */
+  DD_TV_PATH_FULLDIM = 2 /* undecomposed primal-dual iteration, N = 1 (Section 5 "CP")  */
+} dd_tv_path;
+
+typedef struct {
+  int height, width;      /* H, W > 0                                                      */
+  int sub_rows, sub_cols; /* 1 <= sub_rows <= H, 1 <= sub_cols <= W (Section 2.4)          */
+  int fidelity;           /* dd_tv_fidelity                                                */
+  double alpha;           /* > 0 (eq. model)                                               */
+  double c1, c2;          /* DD_TV_SEG region constants (eq. CCV)                           */
+  int outer_iters;        /* >= 0: outer iterations run by dd_tv_solve*                      */
+  int inner_iters;        /* 1..DD_TV_MAX_INNER: local iterations per outer iteration         */
+  double tau, sigma;      /* outer steps, tau sigma <= 1/2 (Algorithm 1; Section 5 uses
+                             tau = 50, sigma tau = 1/2; tau = 1 for segmentation)           */
+  double tau0, sigma0;    /* initial local steps on p and u (Section 5: 10 and 1/80)         */
+  double gamma;           /* local acceleration, 0 < gamma <= 1/tau (Section 5: 1/(8 tau))   */
+  double outer_tol;       /* > 0: stop once (J(u^n) - energy_ref)/|energy_ref| <= outer_tol  */
+  double energy_ref;      /* J* used by outer_tol (eq. stop_outer)                           */
+  int energy_every;       /* with outer_tol: evaluate J every energy_every outer iterations  */
+  int path;               /* dd_tv_path                                                    */
+} dd_tv_params;
+
+#define DD_TV_MAX_INNER 1024
+
+typedef struct {
+  int outer_done;         /* outer iterations run by the call                              */
+  long long pixel_iters;  /* H * W * inner_iters * outer_done (inner work units)            */
+  double energy;          /* J(u) at exit; NaN when not evaluated                          */
+  double rel_err;         /* (energy - energy_ref)/|energy_ref|; NaN when not evaluated     */
+  double ms;              /* device time of the outer iterations (CUDA events)             */
+  int converged;          /* 1 if outer_tol was reached                                    */
+} dd_tv_stats;
+
+/* Fills p with the paper's experimental settings (Section 5): tau = 50,
+ * sigma = 1/(2 tau), tau0 = 10, sigma0 = 1/80, gamma = 1/(8 tau), inner_iters = 10,
+ * fidelity L2, alpha = 10, one subdomain, the fused path, no outer_tol. */
+void dd_tv_default_params(dd_tv_params* p);
+
+/* Validates p and allocates the device state for one H x W problem.  *out is set to
+ * a new handle (or NULL on error).  Must be called with the target device current. */
+int dd_tv_create(dd_tv** out, const dd_tv_params* p);
+
+/* Frees the handle and its device memory.  NULL-safe. */
+int dd_tv_destroy(dd_tv* h);
+
+/* Human-readable description of the last error on h (static string for h == NULL). */
+const char* dd_tv_last_error(const dd_tv* h);
+
+/* Sets the stream (a cudaStream_t, 0 = legacy default) all later work is issued on. */
+int dd_tv_set_stream(dd_tv* h, void* stream);
+
+/* Full solve from host memory: copies f_host (and mask_host, nullable) to the device,
+ * initialises the state (u^0 = f with f := 0 on D, or 1/2 for DD_TV_SEG; p~ = 0,
+ * lambda = 0), runs outer_iters outer iterations (or until outer_tol), copies u to
+ * u_host.  stats is nullable.  Synchronous. */
+int dd_tv_solve(dd_tv* h, const float* f_host, const uint8_t* mask_host, float* u_host, dd_tv_stats* stats);
+
+/* The same with device buffers; asynchronous on the handle's stream unless
+ * stats != NULL or outer_tol > 0 (both need host-side values). */
+int dd_tv_solve_device(dd_tv* h, const float* f_dev, const uint8_t* mask_dev, float* u_dev, dd_tv_stats* stats);
+
+/* Stepping interface.  dd_tv_load copies f (and mask) from device memory into the
+ * handle and initialises the state as dd_tv_solve does; dd_tv_iterate runs n_outer
+ * outer iterations on the resident state (asynchronous); dd_tv_get_u copies the
+ * current u to u_dev. */
+int dd_tv_load(dd_tv* h, const float* f_dev, const uint8_t* mask_dev);
+int dd_tv_iterate(dd_tv* h, int n_outer);
+int dd_tv_get_u(dd_tv* h, float* u_dev);
+
+/* Number of outer iterations run since the last dd_tv_load / dd_tv_set_state. */
+int dd_tv_outer_count(const dd_tv* h);
+
+/* State exchange in the torn layout (device buffers, float32, caller-allocated):
+ *   u     H x W
+ *   P1    (H + sub_rows) x W      tile row a owns rows r0(a)+a .. r0(a+1)+a: the
+ *                                 normal components (oriented down) on the horizontal
+ *                                 edges of that tile row, its top and bottom sides
+ *                                 included (0 on the image boundary)
+ *   P2    H x (W + sub_cols)      tile column b owns columns c0(b)+b .. c0(b+1)+b
+ *                                 (normal components oriented right)
+ *   lamh  (sub_rows - 1) x W      multiplier of the edge between tile rows a, a+1
+ *   lamv  (sub_cols - 1) x H      multiplier of the edge between tile columns b, b+1
+ *   P1prev, P2prev                p~^{n-1} in the P1/P2 layout (only its interface
+ *                                 values are used; get writes zeros elsewhere)
+ * Pointers for empty arrays (e.g. lamh with sub_rows = 1) may be NULL.  For the
+ * full-dimension path P1/P2 hold the global field (sub grid 1 x 1) and P1prev/P2prev
+ * the extrapolated field pbar. */
+int dd_tv_get_state(dd_tv* h, float* u, float* P1, float* P2, float* lamh, float* lamv, float* P1prev,
+                    float* P2prev);
+int dd_tv_set_state(dd_tv* h, const float* u, const float* P1, const float* P2, const float* lamh,
+                    const float* lamv, const float* P1prev, const float* P2prev, int outer_count);
+
+/* J(u) = alpha F(u) + TV(u) (eq. model) of a device image u_dev against the data
+ * f_dev / mask_dev (mask nullable) with the handle's fidelity, alpha, c1, c2.  Kahan-
+ * compensated float32 per thread, float64 across threads and blocks, fixed order
+ * (deterministic).  Synchronous; writes *J_out. */
+int dd_tv_energy(dd_tv* h, const float* u_dev, const float* f_dev, const uint8_t* mask_dev, double* J_out);
+
+/* Energy of the current iterate and the dual value of the averaged dual field
+ * (duality-gap certificate: d <= J* <= J): L2 without mask:
+ * -(1/(2 alpha)) ||div p + alpha f||^2 + (alpha/2) ||f||^2; SEG: sum min(0, alpha g -
+ * div p); otherwise *D_out = -inf.  Synchronous. */
+int dd_tv_gap(dd_tv* h, double* J_out, double* D_out);
+
+
+/* Energy J(u) of the current iterate (the quantity of the outer stopping rule,
+ * eq. stop_outer).  Synchronous. */
+int dd_tv_current_energy(dd_tv* h, double* J_out);
+
+/* ---- Measurement hooks (no counterpart in the paper). ----
+ * dd_tv_set_profiling(h, 1): later dd_tv_iterate / energy calls launch their kernels
+ * directly (no graph replay) and bracket every phase with CUDA events on the
+ * handle's stream.  dd_tv_profile_read synchronises and writes, for each phase
+ * (0 = interface multiplier update, 1 = local solves, 2 = energy reduction), the
+ * summed device time in milliseconds and the number of kernel launches since
+ * profiling was switched on (arrays of 3; either pointer may be NULL); it then
+ * resets the counters.  dd_tv_set_profiling(h, 0) returns to graph replay. */
+int dd_tv_set_profiling(dd_tv* h, int on);
+int dd_tv_profile_read(dd_tv* h, double* ms, long long* launches);
+
+/* Measures the shared-memory load bandwidth of the current device (bytes per second
+ * summed over all SMs) with a streaming ld.shared loop, for use as the roofline
+ * denominator of the fused local solver.  Synchronous; allocates and frees its own
+ * small device buffer.  *gbs_out is in GB/s (1e9 bytes/s). */
+int dd_tv_measure_smem_bandwidth(double* gbs_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DD_TV_H */

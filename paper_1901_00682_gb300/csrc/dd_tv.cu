@@ -1,0 +1,661 @@
+// Host side of the dd_tv C ABI (include/dd_tv.h): argument validation, device
+// state, the outer loop of Algorithm 1 on the three paths, CUDA-graph replay of the
+// outer loop, state exchange and the energy/gap calls.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/dd_tv.h"
+#include "internal.cuh"
+
+using namespace ddtv;
+
+namespace {
+
+constexpr int kGraphChunk = 4;  // outer iterations per captured graph (even: parity is preserved)
+
+// message of the last failed dd_tv_create on this thread (no handle exists then)
+thread_local char g_create_err[512] = {0};
+
+}  // namespace
+
+struct dd_tv {
+  dd_tv_params p;
+  Grid g;            // decomposition grid (1 x 1 for the full-dimension path)
+  int fid;
+  cudaStream_t stream = nullptr;   // where work is issued: the caller's stream or `own`
+  cudaStream_t own = nullptr;      // private blocking stream (orders with the legacy stream)
+  int device = 0;
+  char err[512] = {0};
+  int n = 0;         // outer iterations since load / set_state
+  bool loaded = false;
+  bool has_mask = false;
+
+  size_t npx = 0, n1 = 0, n2 = 0, nh = 0, nv = 0;
+  float *f = nullptr, *u = nullptr, *P1 = nullptr, *P2 = nullptr, *lamh = nullptr, *lamv = nullptr;
+  uint8_t* mask = nullptr;
+  float* strip_mem = nullptr;
+  Strips strips[2] = {};
+  Coef* coef = nullptr;
+  // plain path: phat and pbar; full-dimension path: pbar (carried across iterations)
+  float *Ph1 = nullptr, *Ph2 = nullptr, *Pb1 = nullptr, *Pb2 = nullptr;
+  double* partials = nullptr;
+  unsigned int* counter = nullptr;
+  double* red_out = nullptr;
+  int* flag = nullptr;
+
+  cudaGraphExec_t chunk[2] = {nullptr, nullptr};  // kGraphChunk outer iterations from parity 0 / 1
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  // measurement hooks: event pairs bracketing each phase while profiling is on
+  struct Mark {
+    cudaEvent_t a, b;
+    int slot;
+  };
+  bool prof = false;
+  std::vector<Mark> marks;
+  long long prof_launches[3] = {0, 0, 0};
+};
+
+namespace {
+
+int fail(dd_tv* h, int code, const char* fmt, ...) {
+  if (h) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(h->err, sizeof(h->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define CK(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return fail(h, DD_TV_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+int dalloc(dd_tv* h, T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) return DD_TV_OK;
+  cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    return fail(h, DD_TV_ENOMEM, "cudaMalloc(%zu bytes): %s", count * sizeof(T), cudaGetErrorString(e));
+  }
+  return DD_TV_OK;
+}
+
+int validate(const dd_tv_params* p, char* msg, size_t len) {
+#define BAD(...) (snprintf(msg, len, __VA_ARGS__), DD_TV_EINVAL)
+  if (!p) return BAD("params is NULL");
+  if (p->height < 1 || p->width < 1) return BAD("height and width must be >= 1 (got %d x %d)", p->height, p->width);
+  if ((long long)p->height * p->width > (1LL << 31) - 1) return BAD("image larger than 2^31 - 1 pixels");
+  if (p->path < DD_TV_PATH_FUSED || p->path > DD_TV_PATH_FULLDIM) return BAD("unknown path %d", p->path);
+  if (p->path != DD_TV_PATH_FULLDIM) {
+    if (p->sub_rows < 1 || p->sub_rows > p->height) return BAD("sub_rows must be in [1, height] (got %d)", p->sub_rows);
+    if (p->sub_cols < 1 || p->sub_cols > p->width) return BAD("sub_cols must be in [1, width] (got %d)", p->sub_cols);
+  }
+  if (p->fidelity < DD_TV_L2 || p->fidelity > DD_TV_SEG) return BAD("unknown fidelity %d", p->fidelity);
+  if (!(p->alpha > 0.0) || !std::isfinite(p->alpha)) return BAD("alpha must be finite and > 0");
+  if (p->fidelity == DD_TV_SEG && !(std::isfinite(p->c1) && std::isfinite(p->c2))) return BAD("c1, c2 must be finite");
+  if (p->outer_iters < 0) return BAD("outer_iters must be >= 0");
+  if (p->inner_iters < 1 || p->inner_iters > DD_TV_MAX_INNER)
+    return BAD("inner_iters must be in [1, %d] (got %d)", DD_TV_MAX_INNER, p->inner_iters);
+  if (!(p->tau0 > 0.0) || !(p->sigma0 > 0.0) || !std::isfinite(p->tau0) || !std::isfinite(p->sigma0))
+    return BAD("tau0 and sigma0 must be finite and > 0");
+  // ||div||^2 <= 8 on the pixel grid: tau0 sigma0 ||div||^2 <= 1
+  if (p->tau0 * p->sigma0 > 0.125 * (1.0 + 1e-12)) return BAD("tau0 * sigma0 must be <= 1/8");
+  if (p->path != DD_TV_PATH_FULLDIM) {
+    if (!(p->tau > 0.0) || !(p->sigma > 0.0) || !std::isfinite(p->tau) || !std::isfinite(p->sigma))
+      return BAD("tau and sigma must be finite and > 0");
+    // ||B||^2 = 2: tau sigma ||B||^2 <= 1 (Algorithm 1 asks tau sigma < 1/2; Section 5 uses 1/2)
+    if (p->tau * p->sigma > 0.5 * (1.0 + 1e-12)) return BAD("tau * sigma must be <= 1/2");
+    if (!(p->gamma > 0.0) || p->gamma > 1.0 / p->tau * (1.0 + 1e-12))
+      return BAD("gamma must be in (0, 1/tau]: the local G^* is only (1/tau)-uniformly convex");
+  }
+  if (p->outer_tol < 0.0 || !std::isfinite(p->outer_tol)) return BAD("outer_tol must be finite and >= 0");
+  if (p->outer_tol > 0.0) {
+    if (!std::isfinite(p->energy_ref) || p->energy_ref == 0.0) return BAD("outer_tol needs a finite nonzero energy_ref");
+    if (p->energy_every < 1) return BAD("outer_tol needs energy_every >= 1");
+  }
+  return DD_TV_OK;
+#undef BAD
+}
+
+void build_schedule(const dd_tv_params& p, std::vector<Coef>& c) {
+  const int K = p.inner_iters;
+  c.resize(K);
+  const double a = p.alpha;
+  if (p.path == DD_TV_PATH_FULLDIM) {
+    // plain primal-dual iteration: constant steps, theta = 1, no proximal term
+    const double s = p.sigma0, t = p.tau0;
+    for (int k = 0; k < K; ++k)
+      c[k] = Coef{(float)s, (float)(1.0 / (1.0 + s * a)), (float)(s * a / (1.0 + s * a)), (float)(s * a), 1.0f,
+                  (float)t, 0.0f, 1.0f};
+    return;
+  }
+  // accelerated local iteration, restarted at every outer iteration
+  double tk = p.tau0, sk = p.sigma0;
+  const double tau = p.tau;
+  for (int k = 0; k < K; ++k) {
+    const double th = 1.0 / std::sqrt(1.0 + 2.0 * p.gamma * tk);
+    c[k] = Coef{(float)sk,
+                (float)(1.0 / (1.0 + sk * a)),
+                (float)(sk * a / (1.0 + sk * a)),
+                (float)(sk * a),
+                (float)(tau / (tau + tk)),
+                (float)(tau * tk / (tau + tk)),
+                (float)(tk / (tau + tk)),
+                (float)th};
+    tk = th * tk;
+    sk = sk / th;
+  }
+}
+
+LocalArgs local_args(dd_tv* h, int write_set) {
+  LocalArgs a;
+  a.g = h->g;
+  a.K = h->p.inner_iters;
+  a.tau = (float)h->p.tau;
+  a.c1 = (float)h->p.c1;
+  a.c2 = (float)h->p.c2;
+  a.f = h->f;
+  a.mask = h->has_mask ? h->mask : nullptr;
+  a.u = h->u;
+  a.P1 = h->P1;
+  a.P2 = h->P2;
+  a.lamh = h->lamh;
+  a.lamv = h->lamv;
+  a.out = h->strips[write_set];
+  a.coef = h->coef;
+  return a;
+}
+
+// Phase brackets for the measurement hooks (no-ops unless profiling is on).
+struct PhaseMark {
+  dd_tv* h;
+  int slot;
+  cudaEvent_t a = nullptr;
+  PhaseMark(dd_tv* h_, int slot_, int launches) : h(h_), slot(slot_) {
+    if (!h->prof) return;
+    h->prof_launches[slot] += launches;
+    if (cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, h->stream);
+  }
+  ~PhaseMark() {
+    if (!h->prof || !a) return;
+    cudaEvent_t b = nullptr;
+    if (cudaEventCreate(&b) == cudaSuccess) {
+      cudaEventRecord(b, h->stream);
+      h->marks.push_back(dd_tv::Mark{a, b, slot});
+    } else {
+      cudaEventDestroy(a);
+    }
+  }
+};
+
+// One outer iteration starting from parity `par` (= n mod 2): the strips of p~^n are
+// in set par, those of p~^{n-1} in set 1 - par, and p~^{n+1}'s go to set 1 - par.
+cudaError_t outer_once(dd_tv* h, int par) {
+  cudaError_t e;
+  const cudaStream_t st = h->stream;
+  if (h->p.path == DD_TV_PATH_FULLDIM) {
+    LocalArgs a = local_args(h, 0);
+    PhaseMark m(h, 1, 2 * a.K);
+    for (int k = 0; k < a.K; ++k) {
+      if ((e = launch_plain_ustep(a, h->Pb1, h->Pb2, h->coef + k, h->fid, st)) != cudaSuccess) return e;
+      if ((e = launch_plain_pstep(a, nullptr, nullptr, h->Pb1, h->Pb2, h->coef + k, false, st)) != cudaSuccess)
+        return e;
+    }
+    return cudaSuccess;
+  }
+  {
+    PhaseMark m(h, 0, (h->nh + h->nv) ? 1 : 0);
+    if ((e = launch_interface(h->g, (float)h->p.sigma, h->strips[par], h->strips[1 - par], h->lamh, h->lamv, st)) !=
+        cudaSuccess)
+      return e;
+  }
+  LocalArgs a = local_args(h, 1 - par);
+  if (h->p.path == DD_TV_PATH_FUSED) {
+    PhaseMark m(h, 1, 1);
+    return launch_fused_local(a, h->fid, st);
+  }
+  PhaseMark m(h, 1, 1 + 2 * a.K + ((h->nh + h->nv) ? 1 : 0));
+  if ((e = launch_plain_phat(a, h->Ph1, h->Ph2, h->Pb1, h->Pb2, st)) != cudaSuccess) return e;
+  for (int k = 0; k < a.K; ++k) {
+    if ((e = launch_plain_ustep(a, h->Pb1, h->Pb2, h->coef + k, h->fid, st)) != cudaSuccess) return e;
+    if ((e = launch_plain_pstep(a, h->Ph1, h->Ph2, h->Pb1, h->Pb2, h->coef + k, k + 1 == a.K, st)) != cudaSuccess)
+      return e;
+  }
+  return cudaSuccess;
+}
+
+void drop_graphs(dd_tv* h) {
+  for (auto& g : h->chunk)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+int capture_chunk(dd_tv* h, int par) {
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int q = 0; q < kGraphChunk && e == cudaSuccess; ++q) e = outer_once(h, (par + q) & 1);
+  cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(h, DD_TV_ECUDA, "graph capture failed: %s",
+                cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  e = cudaGraphInstantiate(&h->chunk[par], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    h->chunk[par] = nullptr;
+    return fail(h, DD_TV_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  }
+  return DD_TV_OK;
+}
+
+int run_outer(dd_tv* h, int count) {
+  int done = 0;
+  while (done < count) {
+    const int par = h->n & 1;
+    if (count - done >= kGraphChunk && !h->prof) {
+      if (!h->chunk[par]) {
+        int rc = capture_chunk(h, par);
+        if (rc) return rc;
+      }
+      CK(cudaGraphLaunch(h->chunk[par], h->stream));
+      h->n += kGraphChunk;
+      done += kGraphChunk;
+    } else {
+      CK(outer_once(h, par));
+      h->n += 1;
+      done += 1;
+    }
+  }
+  return DD_TV_OK;
+}
+
+int reset_state(dd_tv* h) {
+  const cudaStream_t st = h->stream;
+  CK(launch_init_u(h->g, h->fid, h->f, h->has_mask ? h->mask : nullptr, h->u, st));
+  CK(cudaMemsetAsync(h->P1, 0, h->n1 * sizeof(float), st));
+  CK(cudaMemsetAsync(h->P2, 0, h->n2 * sizeof(float), st));
+  if (h->nh) CK(cudaMemsetAsync(h->lamh, 0, h->nh * sizeof(float), st));
+  if (h->nv) CK(cudaMemsetAsync(h->lamv, 0, h->nv * sizeof(float), st));
+  if (h->strip_mem) CK(cudaMemsetAsync(h->strip_mem, 0, 4 * (h->nh + h->nv) * sizeof(float), st));
+  if (h->Pb1) {
+    CK(cudaMemsetAsync(h->Pb1, 0, h->n1 * sizeof(float), st));
+    CK(cudaMemsetAsync(h->Pb2, 0, h->n2 * sizeof(float), st));
+  }
+  h->n = 0;
+  h->loaded = true;
+  return DD_TV_OK;
+}
+
+int energy_of(dd_tv* h, const float* u, const float* f, const uint8_t* mask, bool dual, double* out2) {
+  {
+    PhaseMark m(h, 2, 1);
+    CK(launch_energy(h->g, h->fid, (float)h->p.alpha, (float)h->p.c1, (float)h->p.c2, u, f, mask,
+                   dual ? h->P1 : nullptr, dual ? h->P2 : nullptr, h->partials, h->counter, h->red_out, h->stream));
+  }
+  CK(cudaMemcpyAsync(out2, h->red_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return DD_TV_OK;
+}
+
+int solve_loaded(dd_tv* h, dd_tv_stats* stats, bool sync_needed) {
+  const dd_tv_params& p = h->p;
+  const bool tol = p.outer_tol > 0.0;
+  if (stats) {
+    stats->outer_done = 0;
+    stats->pixel_iters = 0;
+    stats->energy = NAN;
+    stats->rel_err = NAN;
+    stats->ms = NAN;
+    stats->converged = 0;
+  }
+  CK(cudaEventRecord(h->ev0, h->stream));
+  int done = 0, rc;
+  bool conv = false;
+  double J = NAN;
+  if (!tol) {
+    if ((rc = run_outer(h, p.outer_iters))) return rc;
+    done = p.outer_iters;
+  } else {
+    while (done < p.outer_iters && !conv) {
+      const int step = std::min(p.energy_every, p.outer_iters - done);
+      if ((rc = run_outer(h, step))) return rc;
+      done += step;
+      double o[2];
+      if ((rc = energy_of(h, h->u, h->f, h->has_mask ? h->mask : nullptr, false, o))) return rc;
+      J = o[0];
+      conv = (J - p.energy_ref) / std::fabs(p.energy_ref) <= p.outer_tol;
+    }
+  }
+  CK(cudaEventRecord(h->ev1, h->stream));
+  if (stats || sync_needed) CK(cudaEventSynchronize(h->ev1));
+  CK(cudaGetLastError());
+  if (stats) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    stats->outer_done = done;
+    stats->pixel_iters = (long long)p.height * p.width * p.inner_iters * (long long)done;
+    stats->energy = J;
+    stats->rel_err = std::isnan(J) ? NAN : (J - p.energy_ref) / std::fabs(p.energy_ref);
+    stats->ms = ms;
+    stats->converged = conv ? 1 : 0;
+  }
+  if (tol && !conv) return fail(h, DD_TV_ENOTCONV, "outer_tol %.3g not reached in %d outer iterations", p.outer_tol, done);
+  return DD_TV_OK;
+}
+
+int load_common(dd_tv* h, const float* f, const uint8_t* mask, cudaMemcpyKind kind) {
+  if (!h) return DD_TV_EINVAL;
+  if (!f) return fail(h, DD_TV_EINVAL, "f is NULL");
+  if (mask && h->fid == DD_TV_SEG) return fail(h, DD_TV_EINVAL, "an inpainting mask is not defined for DD_TV_SEG");
+  CK(cudaMemcpyAsync(h->f, f, h->npx * sizeof(float), kind, h->stream));
+  h->has_mask = mask != nullptr;
+  if (mask) {
+    if (!h->mask) {
+      int rc = dalloc(h, &h->mask, h->npx);
+      if (rc) return rc;
+      drop_graphs(h);
+    }
+    CK(cudaMemcpyAsync(h->mask, mask, h->npx, kind, h->stream));
+  }
+  drop_graphs(h);  // the mask pointer captured in the graphs may have changed
+  return reset_state(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+void dd_tv_default_params(dd_tv_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->height = p->width = 1;
+  p->sub_rows = p->sub_cols = 1;
+  p->fidelity = DD_TV_L2;
+  p->alpha = 10.0;
+  p->outer_iters = 100;
+  p->inner_iters = 10;
+  p->tau = 50.0;
+  p->sigma = 1.0 / (2.0 * 50.0);
+  p->tau0 = 10.0;
+  p->sigma0 = 1.0 / 80.0;
+  p->gamma = 1.0 / (8.0 * 50.0);
+  p->outer_tol = 0.0;
+  p->energy_ref = NAN;
+  p->energy_every = 5;
+  p->path = DD_TV_PATH_FUSED;
+}
+
+int dd_tv_create(dd_tv** out, const dd_tv_params* p) {
+  if (!out) return DD_TV_EINVAL;
+  *out = nullptr;
+  dd_tv* h = new (std::nothrow) dd_tv();
+  if (!h) return DD_TV_ENOMEM;
+  int rc = validate(p, h->err, sizeof(h->err));
+  if (rc) {
+    std::snprintf(g_create_err, sizeof(g_create_err), "%s", h->err);
+    delete h;
+    return rc;
+  }
+  h->p = *p;
+  h->fid = p->fidelity;
+  const bool full = p->path == DD_TV_PATH_FULLDIM;
+  h->g = Grid{p->height, p->width, full ? 1 : p->sub_rows, full ? 1 : p->sub_cols};
+  if (p->path == DD_TV_PATH_FUSED) {
+    const int mr = (h->g.H + h->g.NR - 1) / h->g.NR, mc = (h->g.W + h->g.NC - 1) / h->g.NC;
+    int maxr, maxc;
+    fused_max_tile(&maxr, &maxc);
+    if (mr > maxr || mc > maxc) {
+      fail(h, DD_TV_EUNSUPPORTED, "fused path supports tiles up to %d x %d (got %d x %d)", maxr, maxc, mr, mc);
+      std::snprintf(g_create_err, sizeof(g_create_err), "%s", h->err);
+      delete h;
+      return DD_TV_EUNSUPPORTED;
+    }
+  }
+  cudaGetDevice(&h->device);
+  const Grid& g = h->g;
+  h->npx = (size_t)g.H * g.W;
+  h->n1 = (size_t)(g.H + g.NR) * g.W;
+  h->n2 = (size_t)g.H * (g.W + g.NC);
+  h->nh = (size_t)(g.NR - 1) * g.W;
+  h->nv = (size_t)(g.NC - 1) * g.H;
+  std::vector<Coef> sched;
+  build_schedule(*p, sched);
+  if ((rc = dalloc(h, &h->f, h->npx)) || (rc = dalloc(h, &h->u, h->npx)) || (rc = dalloc(h, &h->P1, h->n1)) ||
+      (rc = dalloc(h, &h->P2, h->n2)) || (rc = dalloc(h, &h->lamh, h->nh)) || (rc = dalloc(h, &h->lamv, h->nv)) ||
+      (rc = dalloc(h, &h->strip_mem, 4 * (h->nh + h->nv))) || (rc = dalloc(h, &h->coef, sched.size())) ||
+      (rc = dalloc(h, &h->partials, (size_t)reduce_partials_count())) || (rc = dalloc(h, &h->counter, 1)) ||
+      (rc = dalloc(h, &h->red_out, 2)) || (rc = dalloc(h, &h->flag, 1))) {
+    std::snprintf(g_create_err, sizeof(g_create_err), "%s", h->err);
+    dd_tv_destroy(h);
+    return rc;
+  }
+  if (p->path != DD_TV_PATH_FUSED) {
+    if ((rc = dalloc(h, &h->Pb1, h->n1)) || (rc = dalloc(h, &h->Pb2, h->n2))) {
+      dd_tv_destroy(h);
+      return rc;
+    }
+  }
+  if (p->path == DD_TV_PATH_PLAIN) {
+    if ((rc = dalloc(h, &h->Ph1, h->n1)) || (rc = dalloc(h, &h->Ph2, h->n2))) {
+      dd_tv_destroy(h);
+      return rc;
+    }
+  }
+  // strip sets: [SB | ST | SR | SL] each, both sets in one allocation (float4-aligned
+  // when W and H are multiples of 4)
+  for (int s = 0; s < 2; ++s) {
+    float* base = h->strip_mem ? h->strip_mem + (size_t)s * 2 * (h->nh + h->nv) : nullptr;
+    h->strips[s].SB = base;
+    h->strips[s].ST = base ? base + h->nh : nullptr;
+    h->strips[s].SR = base ? base + 2 * h->nh : nullptr;
+    h->strips[s].SL = base ? base + 2 * h->nh + h->nv : nullptr;
+  }
+  cudaError_t e;
+  if ((e = cudaMemcpy(h->coef, sched.data(), sched.size() * sizeof(Coef), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(h->counter, 0, sizeof(unsigned int))) != cudaSuccess ||
+      (e = cudaEventCreate(&h->ev0)) != cudaSuccess || (e = cudaEventCreate(&h->ev1)) != cudaSuccess ||
+      (e = cudaStreamCreate(&h->own)) != cudaSuccess) {
+    std::snprintf(g_create_err, sizeof(g_create_err), "dd_tv_create: %s", cudaGetErrorString(e));
+    dd_tv_destroy(h);
+    return DD_TV_ECUDA;
+  }
+  h->stream = h->own;
+  *out = h;
+  return DD_TV_OK;
+}
+
+int dd_tv_destroy(dd_tv* h) {
+  if (!h) return DD_TV_OK;
+  drop_graphs(h);
+  for (auto& m : h->marks) {
+    cudaEventDestroy(m.a);
+    cudaEventDestroy(m.b);
+  }
+  void* bufs[] = {h->f, h->u, h->P1, h->P2, h->lamh, h->lamv, h->mask, h->strip_mem, h->coef, h->Ph1, h->Ph2,
+                  h->Pb1, h->Pb2, h->partials, h->counter, h->red_out, h->flag};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->own) cudaStreamDestroy(h->own);
+  delete h;
+  return DD_TV_OK;
+}
+
+const char* dd_tv_last_error(const dd_tv* h) {
+  if (!h) return g_create_err[0] ? g_create_err : "invalid handle (NULL)";
+  return h->err;
+}
+
+int dd_tv_set_stream(dd_tv* h, void* stream) {
+  if (!h) return DD_TV_EINVAL;
+  h->stream = stream ? (cudaStream_t)stream : h->own;
+  return DD_TV_OK;
+}
+
+int dd_tv_load(dd_tv* h, const float* f_dev, const uint8_t* mask_dev) {
+  return load_common(h, f_dev, mask_dev, cudaMemcpyDeviceToDevice);
+}
+
+int dd_tv_iterate(dd_tv* h, int n_outer) {
+  if (!h) return DD_TV_EINVAL;
+  if (!h->loaded) return fail(h, DD_TV_EINVAL, "no data loaded (dd_tv_load or dd_tv_set_state first)");
+  if (n_outer < 0) return fail(h, DD_TV_EINVAL, "n_outer must be >= 0");
+  return run_outer(h, n_outer);
+}
+
+int dd_tv_outer_count(const dd_tv* h) { return h ? h->n : -1; }
+
+int dd_tv_get_u(dd_tv* h, float* u_dev) {
+  if (!h) return DD_TV_EINVAL;
+  if (!u_dev) return fail(h, DD_TV_EINVAL, "u is NULL");
+  CK(cudaMemcpyAsync(u_dev, h->u, h->npx * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  return DD_TV_OK;
+}
+
+int dd_tv_solve(dd_tv* h, const float* f_host, const uint8_t* mask_host, float* u_host, dd_tv_stats* stats) {
+  if (!h) return DD_TV_EINVAL;
+  if (!u_host) return fail(h, DD_TV_EINVAL, "u is NULL");
+  int rc = load_common(h, f_host, mask_host, cudaMemcpyHostToDevice);
+  if (rc) return rc;
+  rc = solve_loaded(h, stats, true);
+  if (rc && rc != DD_TV_ENOTCONV) return rc;
+  CK(cudaMemcpyAsync(u_host, h->u, h->npx * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return rc;
+}
+
+int dd_tv_solve_device(dd_tv* h, const float* f_dev, const uint8_t* mask_dev, float* u_dev, dd_tv_stats* stats) {
+  if (!h) return DD_TV_EINVAL;
+  if (!u_dev) return fail(h, DD_TV_EINVAL, "u is NULL");
+  int rc = load_common(h, f_dev, mask_dev, cudaMemcpyDeviceToDevice);
+  if (rc) return rc;
+  rc = solve_loaded(h, stats, false);
+  if (rc && rc != DD_TV_ENOTCONV) return rc;
+  CK(cudaMemcpyAsync(u_dev, h->u, h->npx * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  return rc;
+}
+
+int dd_tv_get_state(dd_tv* h, float* u, float* P1, float* P2, float* lamh, float* lamv, float* P1prev,
+                    float* P2prev) {
+  if (!h) return DD_TV_EINVAL;
+  const cudaStream_t st = h->stream;
+  const auto D2D = cudaMemcpyDeviceToDevice;
+  if (u) CK(cudaMemcpyAsync(u, h->u, h->npx * sizeof(float), D2D, st));
+  if (P1) CK(cudaMemcpyAsync(P1, h->P1, h->n1 * sizeof(float), D2D, st));
+  if (P2) CK(cudaMemcpyAsync(P2, h->P2, h->n2 * sizeof(float), D2D, st));
+  if (lamh && h->nh) CK(cudaMemcpyAsync(lamh, h->lamh, h->nh * sizeof(float), D2D, st));
+  if (lamv && h->nv) CK(cudaMemcpyAsync(lamv, h->lamv, h->nv * sizeof(float), D2D, st));
+  if (h->p.path == DD_TV_PATH_FULLDIM) {
+    if (P1prev) CK(cudaMemcpyAsync(P1prev, h->Pb1, h->n1 * sizeof(float), D2D, st));
+    if (P2prev) CK(cudaMemcpyAsync(P2prev, h->Pb2, h->n2 * sizeof(float), D2D, st));
+    return DD_TV_OK;
+  }
+  if (P1prev && P2prev) {
+    CK(cudaMemsetAsync(P1prev, 0, h->n1 * sizeof(float), st));
+    CK(cudaMemsetAsync(P2prev, 0, h->n2 * sizeof(float), st));
+    CK(launch_scatter_strips(h->g, h->strips[1 - (h->n & 1)], P1prev, P2prev, st));
+  }
+  return DD_TV_OK;
+}
+
+int dd_tv_set_state(dd_tv* h, const float* u, const float* P1, const float* P2, const float* lamh,
+                    const float* lamv, const float* P1prev, const float* P2prev, int outer_count) {
+  if (!h) return DD_TV_EINVAL;
+  if (!u || !P1 || !P2) return fail(h, DD_TV_EINVAL, "u, P1 and P2 are required");
+  if ((h->nh && !lamh) || (h->nv && !lamv)) return fail(h, DD_TV_EINVAL, "multipliers are required");
+  if (!P1prev || !P2prev) return fail(h, DD_TV_EINVAL, "P1prev and P2prev are required");
+  if (outer_count < 0) return fail(h, DD_TV_EINVAL, "outer_count must be >= 0");
+  const cudaStream_t st = h->stream;
+  const auto D2D = cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(h->u, u, h->npx * sizeof(float), D2D, st));
+  CK(cudaMemcpyAsync(h->P1, P1, h->n1 * sizeof(float), D2D, st));
+  CK(cudaMemcpyAsync(h->P2, P2, h->n2 * sizeof(float), D2D, st));
+  if (h->nh) CK(cudaMemcpyAsync(h->lamh, lamh, h->nh * sizeof(float), D2D, st));
+  if (h->nv) CK(cudaMemcpyAsync(h->lamv, lamv, h->nv * sizeof(float), D2D, st));
+  h->n = outer_count;
+  if (h->p.path == DD_TV_PATH_FULLDIM) {
+    CK(cudaMemcpyAsync(h->Pb1, P1prev, h->n1 * sizeof(float), D2D, st));
+    CK(cudaMemcpyAsync(h->Pb2, P2prev, h->n2 * sizeof(float), D2D, st));
+  } else {
+    CK(launch_extract_strips(h->g, P1, P2, h->strips[h->n & 1], st));
+    CK(launch_extract_strips(h->g, P1prev, P2prev, h->strips[1 - (h->n & 1)], st));
+  }
+  h->loaded = true;
+  return DD_TV_OK;
+}
+
+int dd_tv_energy(dd_tv* h, const float* u_dev, const float* f_dev, const uint8_t* mask_dev, double* J_out) {
+  if (!h) return DD_TV_EINVAL;
+  if (!u_dev || !f_dev || !J_out) return fail(h, DD_TV_EINVAL, "u, f and J_out are required");
+  double o[2];
+  int rc = energy_of(h, u_dev, f_dev, mask_dev, false, o);
+  if (rc) return rc;
+  *J_out = o[0];
+  return DD_TV_OK;
+}
+
+int dd_tv_gap(dd_tv* h, double* J_out, double* D_out) {
+  if (!h) return DD_TV_EINVAL;
+  if (!h->loaded) return fail(h, DD_TV_EINVAL, "no data loaded");
+  const bool dual = h->fid == DD_TV_SEG || (h->fid == DD_TV_L2 && !h->has_mask);
+  double o[2];
+  int rc = energy_of(h, h->u, h->f, h->has_mask ? h->mask : nullptr, dual, o);
+  if (rc) return rc;
+  if (J_out) *J_out = o[0];
+  if (D_out) *D_out = dual ? o[1] : -INFINITY;
+  return DD_TV_OK;
+}
+
+int dd_tv_current_energy(dd_tv* h, double* J_out) {
+  if (!h) return DD_TV_EINVAL;
+  if (!h->loaded) return fail(h, DD_TV_EINVAL, "no data loaded");
+  if (!J_out) return fail(h, DD_TV_EINVAL, "J_out is NULL");
+  double o[2];
+  int rc = energy_of(h, h->u, h->f, h->has_mask ? h->mask : nullptr, false, o);
+  if (rc) return rc;
+  *J_out = o[0];
+  return DD_TV_OK;
+}
+
+int dd_tv_set_profiling(dd_tv* h, int on) {
+  if (!h) return DD_TV_EINVAL;
+  h->prof = on != 0;
+  return DD_TV_OK;
+}
+
+int dd_tv_profile_read(dd_tv* h, double* ms, long long* launches) {
+  if (!h) return DD_TV_EINVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (auto& m : h->marks) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, m.a, m.b) == cudaSuccess) acc[m.slot] += t;
+    cudaEventDestroy(m.a);
+    cudaEventDestroy(m.b);
+  }
+  h->marks.clear();
+  for (int s = 0; s < 3; ++s) {
+    if (ms) ms[s] = acc[s];
+    if (launches) launches[s] = h->prof_launches[s];
+    h->prof_launches[s] = 0;
+  }
+  return DD_TV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+// Internal declarations shared by the translation units of the dd_tv library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "pointwise.cuh"
+
+namespace ddtv {
+
+// Image and subdomain grid.
+struct Grid {
+  int H, W, NR, NC;
+};
+
+// Interface strips: the interface values of one torn dual field p~^n.
+//   SB (NR-1) x W : bottom side of tile row a (s-side copy of horizontal interface a)
+//   ST (NR-1) x W : top side of tile row a+1  (t-side copy)
+//   SR (NC-1) x H : right side of tile column b (s-side copy of vertical interface b)
+//   SL (NC-1) x H : left side of tile column b+1 (t-side copy)
+struct Strips {
+  float *SB, *ST, *SR, *SL;
+};
+
+// Arguments of one local-solve launch (fused or plain path).
+struct LocalArgs {
+  Grid g;
+  int K;                 // inner iterations
+  float tau;             // outer tau (proximal centre phat = p~ -+ tau lambda)
+  float c1, c2;          // SEG constants
+  const float* f;        // H x W
+  const uint8_t* mask;   // H x W or nullptr
+  float* u;              // H x W
+  float* P1;             // (H + NR) x W torn
+  float* P2;             // H x (W + NC) torn
+  const float* lamh;     // (NR-1) x W
+  const float* lamv;     // (NC-1) x H
+  Strips out;            // strips of p~^{n+1} (written at the end)
+  const Coef* coef;      // K coefficient sets (device)
+};
+
+// ---- kernels_interface.cu
+// lambda += sigma ((2 cur_s - prev_s) - (2 cur_t - prev_t)) on every interface edge.
+cudaError_t launch_interface(const Grid& g, float sigma, Strips cur, Strips prev, float* lamh, float* lamv,
+                             cudaStream_t st);
+// strips <- interface values of the torn field (P1, P2)
+cudaError_t launch_extract_strips(const Grid& g, const float* P1, const float* P2, Strips s, cudaStream_t st);
+// P1/P2 <- 0 except the interface values, taken from the strips
+cudaError_t launch_scatter_strips(const Grid& g, Strips s, float* P1, float* P2, cudaStream_t st);
+
+// ---- kernels_fused.cu
+// One outer iteration's local solves, all tiles, fused (returns cudaErrorInvalidValue
+// if no fused configuration fits the tile shape).
+cudaError_t launch_fused_local(const LocalArgs& a, int fidelity, cudaStream_t st);
+// Largest tile (rows, cols) the fused kernel supports.
+void fused_max_tile(int* rows, int* cols);
+// Name of the configuration chosen for a tile shape (for reports).
+const char* fused_config_name(int mr, int mc);
+
+// ---- kernels_plain.cu
+// phat = p~ -+ tau lambda on the interface sides, pbar = p~; full arrays.
+cudaError_t launch_plain_phat(const LocalArgs& a, float* Ph1, float* Ph2, float* Pb1, float* Pb2, cudaStream_t st);
+// one u-step over the whole torn field (reads pbar)
+cudaError_t launch_plain_ustep(const LocalArgs& a, const float* Pb1, const float* Pb2, const Coef* ck, int fidelity,
+                               cudaStream_t st);
+// one p-step; phat may be nullptr (no proximal term, full-dimension comparator);
+// write_strips: also write the interface strips of the new p.
+cudaError_t launch_plain_pstep(const LocalArgs& a, const float* Ph1, const float* Ph2, float* Pb1, float* Pb2,
+                               const Coef* ck, bool write_strips, cudaStream_t st);
+
+// ---- kernels_reduce.cu
+// out[0] = J(u) = alpha F(u) + TV(u); out[1] = dual value of the averaged torn field
+// (P1, P2 nullable: then out[1] is not computed).  partials: scratch of
+// reduce_partials_count() doubles; counter: one zeroed unsigned int that the kernel
+// leaves zeroed.
+cudaError_t launch_energy(const Grid& g, int fidelity, float alpha, float c1, float c2, const float* u,
+                          const float* f, const uint8_t* mask, const float* P1, const float* P2, double* partials,
+                          unsigned int* counter, double* out, cudaStream_t st);
+int reduce_partials_count();
+
+// ---- kernels_misc.cu
+// u0 = f (0 on D) for L2/L1, 1/2 for SEG
+cudaError_t launch_init_u(const Grid& g, int fidelity, const float* f, const uint8_t* mask, float* u, cudaStream_t st);
+// global field (H+1) x W / H x (W+1) <-> torn field with a 1 x 1 grid (same arrays)
+}  // namespace ddtv

@@ -1,0 +1,75 @@
+// Pointwise arithmetic of one local primal-dual iteration (Section 5, local
+// solver: the accelerated primal-dual algorithm with the dual field p as the
+// uniformly convex variable).  Every kernel that runs an inner iteration (fused and
+// plain paths, full-dimension comparator) uses these functions, so the paths agree
+// bit for bit.  Compiled with --fmad=false: only the fmaf calls written here fuse.
+#pragma once
+
+#include <cstdint>
+
+namespace ddtv {
+
+enum { FID_L2 = 0, FID_L1 = 1, FID_SEG = 2 };
+
+// Coefficients of inner iteration k, computed on the host in double precision:
+//   sig = sigma_k                       u-step size
+//   ua  = 1 / (1 + sigma_k alpha)       L2 prox: u = ua * ubar + ub * f
+//   ub  = sigma_k alpha / (1 + sigma_k alpha)
+//   s   = sigma_k alpha                 L1 shrink threshold, SEG step on g
+//   pa  = tau / (tau + tau_k)           prox of G^*: p = proj_C(pa p + pc Du + pb phat)
+//   pc  = tau tau_k / (tau + tau_k)
+//   pb  = tau_k / (tau + tau_k)
+//   th  = theta_k = 1 / sqrt(1 + 2 gamma tau_k)   extrapolation pbar = pn + th (pn - p)
+struct Coef {
+  float sig, ua, ub, s, pa, pc, pb, th;
+};
+
+// div_s p at a pixel from the normal components on its four sides
+// (outflow: bottom - top + right - left, Section 2.3)
+__device__ __forceinline__ float div_px(float top, float bot, float left, float right) {
+  return ((bot - top) + right) - left;
+}
+
+// u <- prox_{sigma_k alpha F}(u + sigma_k div pbar) (Section 3 proximity maps).
+// fg is f (L2, L1) or g = (f - c1)^2 - (f - c2)^2 (SEG); in_d marks the inpainting
+// domain D, where the L2/L1 fidelity vanishes and the prox is the identity.
+template <int FID>
+__device__ __forceinline__ float u_update(float u, float d, float fg, bool in_d, const Coef& c) {
+  const float ubar = fmaf(c.sig, d, u);
+  if (FID == FID_SEG) {
+    const float x = fmaf(-c.s, fg, ubar);
+    return fminf(fmaxf(x, 0.0f), 1.0f);
+  }
+  if (in_d) return ubar;
+  if (FID == FID_L2) return fmaf(c.ub, fg, c.ua * ubar);
+  // L1: f + shr(ubar - f, s), shr(v, s) = max(|v| - s, 0) sign(v)
+  const float v = ubar - fg;
+  const float m = fabsf(v) - c.s;
+  return m > 0.0f ? fg + copysignf(m, v) : fg;
+}
+
+// One dof of the p-step: q = p + tau_k Du, p_new = proj_[-1,1]((tau q + tau_k phat) /
+// (tau + tau_k)), pbar = p_new + theta_k (p_new - p).
+__device__ __forceinline__ void p_update(float& p, float& pbar, float du, float phat, const Coef& c) {
+  const float t = fmaf(c.pc, du, fmaf(c.pa, p, c.pb * phat));
+  const float pn = fminf(fmaxf(t, -1.0f), 1.0f);
+  pbar = fmaf(c.th, pn - p, pn);
+  p = pn;
+}
+
+// proximal centre phat = p~^n - tau B^* lambda on an interface side (Algorithm 1):
+// the s-side (bottom/right) copy gets -tau lambda, the t-side (top/left) copy +tau lambda
+__device__ __forceinline__ float phat_s(float p, float lam, float tau) { return fmaf(-tau, lam, p); }
+__device__ __forceinline__ float phat_t(float p, float lam, float tau) { return fmaf(tau, lam, p); }
+
+// first pixel row (column) of tile a when len pixels are split into n tiles
+__host__ __device__ __forceinline__ int part_start(int a, int len, int n) {
+  return (int)(((long long)a * len) / n);
+}
+
+// the tile that pixel row (column) i belongs to
+__host__ __device__ __forceinline__ int part_of(int i, int len, int n) {
+  return (int)(((long long)(i + 1) * n - 1) / len);
+}
+
+}  // namespace ddtv

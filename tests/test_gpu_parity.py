@@ -1,0 +1,219 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same
+seeded inputs, at equal iteration counts.  Bar (stated per result):
+  max |u_gpu - u_oracle| <= 5e-4 on [0, 1]-range images, relative energy error <= 1e-5,
+and bit-exact agreement between the fused and the plain GPU paths (they share the
+pointwise arithmetic).  Covers several tiles with ragged tails, every fidelity, the
+inpainting mask, the 1 x 1 grid, the full-dimension comparator, state export/import
+and, at the 4096^2 / 32 x 32 workload in the benchmark's launch configuration, a
+few outer iterations compared element by element.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U_TOL = 5e-4
+E_TOL = 1e-5
+
+
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_00682_gb300 import _lib
+    _lib.load()
+    return _lib
+
+
+def _run_gpu(f, mask, n_outer, path="fused", **kw):
+    L = _gpu()
+    H, W = f.shape
+    p = L.make_params(H, W, path=path, outer_iters=n_outer, **kw)
+    s = L.Solver(p)
+    fd = torch.from_numpy(np.ascontiguousarray(f, dtype=np.float32)).cuda()
+    md = None if mask is None else torch.from_numpy(np.ascontiguousarray(mask, dtype=np.uint8)).cuda()
+    s.load(fd, md)
+    s.iterate(n_outer)
+    st = s.get_state()
+    torch.cuda.synchronize()
+    return s, {k: v.cpu().numpy().astype(np.float64) for k, v in st.items()}, fd, md
+
+
+def _run_oracle(f, mask, n_outer, sub_rows=1, sub_cols=1, fidelity="l2", alpha=10.0, c1=0.0, c2=0.0,
+                inner_iters=10, tau=None, **_):
+    H, W = f.shape
+    tau = tau if tau is not None else (1.0 if fidelity == "seg" else 50.0)
+    pr = oracle.Problem(H, W, sub_rows, sub_cols, fidelity=fidelity, alpha=alpha, c1=c1, c2=c2, tau=tau,
+                        inner=inner_iters)
+    st = oracle.dd_run(pr, f.astype(np.float64), n_outer, mask=mask)
+    return pr, st
+
+
+def _check(f, mask, n_outer, **kw):
+    s, g, fd, md = _run_gpu(f, mask, n_outer, **kw)
+    pr, o = _run_oracle(f, mask, n_outer, **kw)
+    du = np.abs(g["u"] - o.u).max()
+    assert du <= U_TOL, f"max|du| = {du}"
+    Jg = oracle.energy(pr, g["u"], f.astype(np.float64), mask)
+    Jo = oracle.energy(pr, o.u, f.astype(np.float64), mask)
+    assert abs(Jg - Jo) <= E_TOL * abs(Jo), (Jg, Jo)
+    # the dual field and the multipliers follow the same trajectory
+    assert np.abs(g["P1"] - o.P1).max() <= 1e-2 and np.abs(g["P2"] - o.P2).max() <= 1e-2
+    if o.lamh.size:
+        assert np.abs(g["lamh"] - o.lamh).max() <= 1e-2 * max(1.0, np.abs(o.lamh).max())
+    return s, g, o, du
+
+
+def test_rof128_parity():
+    """ROF 128x128, 2x2 subdomains of 64x64, 200 outer x 10 inner."""
+    f, _ = synth.rof_image(128, 128, 12, 0.05, 0)
+    _check(f, None, 200, sub_rows=2, sub_cols=2, fidelity="l2", alpha=10.0, inner_iters=10)
+
+
+@pytest.mark.parametrize("H,W,NR,NC", [(67, 45, 3, 2), (96, 200, 2, 3), (33, 31, 1, 1), (130, 130, 2, 2),
+                                       (40, 64, 5, 1), (16, 256, 1, 2)])
+def test_ragged_tiles_parity(H, W, NR, NC):
+    f, _ = synth.rof_image(H, W, 6, 0.05, 1)
+    _check(f, None, 30, sub_rows=NR, sub_cols=NC, fidelity="l2", alpha=10.0, inner_iters=7)
+
+
+def test_tvl1_inpainting_parity():
+    f, mask, _ = synth.tvl1_inpaint_image(160, 96, 10, 0.1, 0.2, 2)
+    _check(f, mask, 60, sub_rows=3, sub_cols=2, fidelity="l1", alpha=1.5, inner_iters=10)
+
+
+def test_l2_inpainting_parity():
+    f, _ = synth.rof_image(96, 96, 8, 0.05, 3)
+    mask = synth.bernoulli_mask(f.shape, 0.2, np.random.Generator(np.random.PCG64(5)))
+    f = f.copy()
+    f[mask == 1] = 0.0
+    _check(f, mask, 60, sub_rows=2, sub_cols=2, fidelity="l2", alpha=10.0, inner_iters=10)
+
+
+def test_segmentation_parity():
+    f, _ = synth.seg_image(128, 64, 10, 0.05, 4)
+    _check(f, None, 80, sub_rows=2, sub_cols=1, fidelity="seg", alpha=20.0, c1=0.2, c2=0.8, inner_iters=10)
+
+
+def test_tile_128_parity_with_interfaces():
+    # the 128x128-tile configuration (cluster of CTAs per subdomain) with all four sides active
+    f, _ = synth.rof_image(384, 384, 30, 0.1, 6)
+    _check(f, None, 12, sub_rows=3, sub_cols=3, fidelity="l2", alpha=8.0, inner_iters=10)
+
+
+def test_fused_equals_plain_bitwise():
+    f, mask, _ = synth.tvl1_inpaint_image(96, 80, 8, 0.1, 0.2, 7)
+    kw = dict(sub_rows=3, sub_cols=2, fidelity="l1", alpha=1.5, inner_iters=9)
+    _, a, _, _ = _run_gpu(f, mask, 17, path="fused", **kw)
+    _, b, _, _ = _run_gpu(f, mask, 17, path="plain", **kw)
+    for k in ("u", "P1", "P2", "lamh", "lamv"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_fulldim_parity():
+    f, _ = synth.rof_image(64, 96, 8, 0.05, 8)
+    s, g, _, _ = _run_gpu(f, None, 30, path="fulldim", fidelity="l2", alpha=10.0, inner_iters=10)
+    pr = oracle.Problem(64, 96, fidelity="l2", alpha=10.0)
+    cp = oracle.cp_run(pr, f.astype(np.float64), 300)
+    assert np.abs(g["u"] - cp.u).max() <= U_TOL
+    assert np.abs(g["P1"] - cp.p1).max() <= 1e-2
+
+
+def test_energy_and_gap_kernels():
+    L = _gpu()
+    f, _ = synth.rof_image(257, 131, 10, 0.05, 9)
+    rng = np.random.default_rng(0)
+    u = (f + 0.01 * rng.standard_normal(f.shape)).astype(np.float32)
+    mask = (rng.uniform(size=f.shape) < 0.2).astype(np.uint8)
+    for fid, m in (("l2", None), ("l2", mask), ("l1", mask), ("seg", None)):
+        p = L.make_params(257, 131, 2, 2, fidelity=fid, alpha=7.0, c1=0.2, c2=0.8)
+        s = L.Solver(p)
+        ud = torch.from_numpy(np.clip(u, 0, 1) if fid == "seg" else u).cuda()
+        J = s.energy(ud, torch.from_numpy(f).cuda(), None if m is None else torch.from_numpy(m).cuda())
+        pr = oracle.Problem(257, 131, 2, 2, fidelity=fid, alpha=7.0, c1=0.2, c2=0.8)
+        Jo = oracle.energy(pr, ud.cpu().numpy().astype(np.float64), f.astype(np.float64), m)
+        assert abs(J - Jo) <= 1e-6 * abs(Jo), (fid, J, Jo)
+    # duality gap of a DD iterate: same J and dual value as the oracle on the same state
+    s, g, _, _ = _run_gpu(f, None, 40, sub_rows=2, sub_cols=3, fidelity="l2", alpha=7.0)
+    J, D = s.gap()
+    pr = oracle.Problem(257, 131, 2, 3, alpha=7.0)
+    p1, p2 = oracle.torn_to_global(pr, g["P1"], g["P2"])
+    Do = oracle.dual_value(pr, p1, p2, f.astype(np.float64))
+    Jo = oracle.energy(pr, g["u"], f.astype(np.float64))
+    assert abs(J - Jo) <= 1e-6 * Jo and abs(D - Do) <= 1e-6 * abs(Do)
+    assert D <= J
+
+
+def test_state_roundtrip_resume_is_bit_identical():
+    L = _gpu()
+    f, _ = synth.rof_image(96, 64, 8, 0.05, 10)
+    kw = dict(sub_rows=3, sub_cols=2, fidelity="l2", alpha=10.0)
+    s, a, _, _ = _run_gpu(f, None, 23, **kw)
+    s2, b, fd, _ = _run_gpu(f, None, 11, **kw)
+    st = s2.get_state()
+    s3 = L.Solver(L.make_params(96, 64, **kw))
+    s3.load(fd)
+    s3.set_state(st, 11)
+    s3.iterate(12)
+    c = {k: v.cpu().numpy().astype(np.float64) for k, v in s3.get_state().items()}
+    for k in ("u", "P1", "P2", "lamh", "lamv"):
+        assert np.array_equal(a[k], c[k]), k
+
+
+def test_host_solve_matches_device_path():
+    L = _gpu()
+    f, _ = synth.rof_image(128, 128, 12, 0.05, 0)
+    p = L.make_params(128, 128, 2, 2, outer_iters=37)
+    s = L.Solver(p)
+    u_host, stats, rc = s.solve_host(f)
+    assert rc == L.OK and stats.outer_done == 37 and stats.pixel_iters == 128 * 128 * 10 * 37
+    _, g, _, _ = _run_gpu(f, None, 37, sub_rows=2, sub_cols=2)
+    assert np.array_equal(u_host.astype(np.float64), g["u"])
+
+
+def test_outer_tolerance_stops():
+    L = _gpu()
+    f, _ = synth.rof_image(64, 64, 6, 0.05, 11)
+    pr = oracle.Problem(64, 64, alpha=10.0)
+    Jstar = oracle.energy(pr, oracle.cp_run(pr, f.astype(np.float64), 20000).u, f.astype(np.float64))
+    p = L.make_params(64, 64, 2, 2, outer_iters=2000, outer_tol=1e-4, energy_ref=Jstar, energy_every=5)
+    s = L.Solver(p)
+    u, stats, rc = s.solve_host(f)
+    assert rc == L.OK and stats.converged == 1
+    assert stats.rel_err <= 1e-4 and stats.outer_done % 5 == 0 and stats.outer_done < 2000
+    # one check earlier had not converged
+    p2 = L.make_params(64, 64, 2, 2, outer_iters=stats.outer_done - 5)
+    u2, _, _ = L.Solver(p2).solve_host(f)
+    J2 = oracle.energy(pr, u2.astype(np.float64), f.astype(np.float64))
+    assert (J2 - Jstar) / Jstar > 1e-4
+
+
+def test_errors_are_reported_not_raised_on_device():
+    L = _gpu()
+    s = L.Solver(L.make_params(32, 32, 2, 2))
+    with pytest.raises(L.DDTVError) as e:
+        s.iterate(1)   # nothing loaded
+    assert e.value.code == L.EINVAL
+    with pytest.raises(L.DDTVError):
+        L.Solver(L.make_params(32, 32, 2, 2, fidelity="seg")).load(torch.zeros(32, 32, device="cuda"),
+                                                                  torch.zeros(32, 32, dtype=torch.uint8,
+                                                                              device="cuda"))
+    # tiles larger than the fused kernel supports are refused up front
+    with pytest.raises(L.DDTVError) as e:
+        L.Solver(L.make_params(512, 512, 1, 1))
+    assert e.value.code == L.EUNSUPPORTED
+
+
+@pytest.mark.slow
+def test_full_size_4096_sampled_parity():
+    """4096^2, 32x32 subdomains of 128^2, inner 10, the benchmark's launch
+    configuration: 2 outer iterations, every pixel compared with the oracle."""
+    f, _ = synth.rof_image(4096, 4096, 400, 0.1, 0)
+    kw = dict(sub_rows=32, sub_cols=32, fidelity="l2", alpha=8.0, inner_iters=10)
+    _, g, _, _ = _run_gpu(f, None, 2, **kw)
+    _, o = _run_oracle(f, None, 2, **kw)
+    assert np.abs(g["u"] - o.u).max() <= U_TOL
+    assert np.abs(g["lamh"] - o.lamh).max() <= 1e-3
