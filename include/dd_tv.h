@@ -81,6 +81,9 @@ typedef struct {
   double energy_ref;      /* J* used by outer_tol (eq. stop_outer)                           */
   int energy_every;       /* with outer_tol: evaluate J every energy_every outer iterations  */
   int path;               /* dd_tv_path                                                    */
+  int variant;            /* fused path: hardware mapping of a 128 x 128 subdomain (which
+                             CTA cluster shape and rows per thread), 0 = default; the
+                             arithmetic and results do not depend on it              */
 } dd_tv_params;
 
 #define DD_TV_MAX_INNER 1024

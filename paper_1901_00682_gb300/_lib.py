@@ -31,7 +31,7 @@ class Params(ctypes.Structure):
         ("tau", ctypes.c_double), ("sigma", ctypes.c_double),
         ("tau0", ctypes.c_double), ("sigma0", ctypes.c_double), ("gamma", ctypes.c_double),
         ("outer_tol", ctypes.c_double), ("energy_ref", ctypes.c_double),
-        ("energy_every", ctypes.c_int), ("path", ctypes.c_int),
+        ("energy_every", ctypes.c_int), ("path", ctypes.c_int), ("variant", ctypes.c_int),
     ]
 
 
@@ -118,7 +118,8 @@ def default_params() -> Params:
 
 def make_params(height, width, sub_rows=1, sub_cols=1, fidelity=L2, alpha=10.0, c1=0.0, c2=0.0,
                 outer_iters=100, inner_iters=10, tau=None, sigma=None, tau0=10.0, sigma0=None,
-                gamma=None, outer_tol=0.0, energy_ref=math.nan, energy_every=5, path=PATH_FUSED) -> Params:
+                gamma=None, outer_tol=0.0, energy_ref=math.nan, energy_every=5, path=PATH_FUSED,
+                variant=0) -> Params:
     """Params with the paper's defaults (Section 5) for every unspecified step size:
     tau = 50 (1 for segmentation), sigma = 1/(2 tau), sigma0 = 1/(8 tau0),
     gamma = 1/(8 tau)."""
@@ -135,6 +136,7 @@ def make_params(height, width, sub_rows=1, sub_cols=1, fidelity=L2, alpha=10.0, 
     p.gamma = gamma if gamma is not None else 1.0 / (8.0 * tau)
     p.outer_tol, p.energy_ref, p.energy_every = outer_tol, energy_ref, energy_every
     p.path = {"fused": PATH_FUSED, "plain": PATH_PLAIN, "fulldim": PATH_FULLDIM}.get(path, path)
+    p.variant = variant
     return p
 
 

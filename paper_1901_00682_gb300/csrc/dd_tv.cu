@@ -119,6 +119,8 @@ int validate(const dd_tv_params* p, char* msg, size_t len) {
     if (!(p->gamma > 0.0) || p->gamma > 1.0 / p->tau * (1.0 + 1e-12))
       return BAD("gamma must be in (0, 1/tau]: the local G^* is only (1/tau)-uniformly convex");
   }
+  if (p->path == DD_TV_PATH_FUSED && (p->variant < 0 || p->variant >= fused_num_variants()))
+    return BAD("variant must be in [0, %d)", fused_num_variants());
   if (p->outer_tol < 0.0 || !std::isfinite(p->outer_tol)) return BAD("outer_tol must be finite and >= 0");
   if (p->outer_tol > 0.0) {
     if (!std::isfinite(p->energy_ref) || p->energy_ref == 0.0) return BAD("outer_tol needs a finite nonzero energy_ref");
@@ -223,7 +225,7 @@ cudaError_t outer_once(dd_tv* h, int par) {
   LocalArgs a = local_args(h, 1 - par);
   if (h->p.path == DD_TV_PATH_FUSED) {
     PhaseMark m(h, 1, 1);
-    return launch_fused_local(a, h->fid, st);
+    return launch_fused_local(a, h->fid, h->p.variant, st);
   }
   PhaseMark m(h, 1, 1 + 2 * a.K + ((h->nh + h->nv) ? 1 : 0));
   if ((e = launch_plain_phat(a, h->Ph1, h->Ph2, h->Pb1, h->Pb2, st)) != cudaSuccess) return e;
@@ -427,6 +429,14 @@ int dd_tv_create(dd_tv** out, const dd_tv_params* p) {
     }
   }
   cudaGetDevice(&h->device);
+  if (p->path == DD_TV_PATH_FUSED) {
+    cudaError_t e = fused_prepare();
+    if (e != cudaSuccess) {
+      std::snprintf(g_create_err, sizeof(g_create_err), "fused kernel set-up: %s", cudaGetErrorString(e));
+      delete h;
+      return DD_TV_ECUDA;
+    }
+  }
   const Grid& g = h->g;
   h->npx = (size_t)g.H * g.W;
   h->n1 = (size_t)(g.H + g.NR) * g.W;

@@ -52,11 +52,16 @@ cudaError_t launch_scatter_strips(const Grid& g, Strips s, float* P1, float* P2,
 // ---- kernels_fused.cu
 // One outer iteration's local solves, all tiles, fused (returns cudaErrorInvalidValue
 // if no fused configuration fits the tile shape).
-cudaError_t launch_fused_local(const LocalArgs& a, int fidelity, cudaStream_t st);
+cudaError_t launch_fused_local(const LocalArgs& a, int fidelity, int variant, cudaStream_t st);
+// Sets the shared-memory opt-in of every fused configuration on the current device
+// (called at handle creation, outside any stream capture).
+cudaError_t fused_prepare();
 // Largest tile (rows, cols) the fused kernel supports.
 void fused_max_tile(int* rows, int* cols);
-// Name of the configuration chosen for a tile shape (for reports).
-const char* fused_config_name(int mr, int mc);
+// Number of hardware mappings available for 128 x 128 tiles.
+int fused_num_variants();
+// Name of the configuration chosen for a tile shape and variant (for reports).
+const char* fused_config_name(int mr, int mc, int variant);
 
 // ---- kernels_plain.cu
 // phat = p~ -+ tau lambda on the interface sides, pbar = p~; full arrays.

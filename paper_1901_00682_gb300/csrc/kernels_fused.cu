@@ -1,64 +1,92 @@
 // Fused local solver: all inner iterations of one outer iteration of Algorithm 1 for
 // every subdomain in one launch (Section 5, local problem eq. local, solved by the
 // accelerated primal-dual algorithm with the dual field p as the uniformly convex
-// variable; projection onto the box C of eq. proj_C fused into the p-step).
+// variable; the projection onto the box C of eq. proj_C is fused into the p-step).
 //
 // Mapping.  One subdomain (tile of mr x mc pixels, mc <= BW, mr <= CL*TR*R) is owned
-// by a thread-block cluster of CL CTAs; CTA `rank` of the cluster owns a band of
-// TR*R tile rows, and inside it thread (x, y) owns pixel column x and the R
-// consecutive rows y*R .. y*R+R-1 of the band (lanes of a warp = 32 adjacent
-// columns).  A thread keeps, in registers, for each of its pixels: u, the top-edge
-// and left-edge dofs p1, p2 of the torn dual field, their proximal centres phat and
-// extrapolations pbar, and f (or g for segmentation).  Only the values a neighbour
-// needs go through shared memory: u (read by the right and lower neighbours in the
-// p-step) and pbar2 (read by the left neighbour in the u-step), plus one row per
-// thread row for pbar1 and u at strip ends.  Rows crossing a CTA boundary are
-// pushed into the neighbour CTA's shared memory (distributed shared memory) before
-// the cluster barrier.  Two barriers per inner iteration (after the u-step and after
-// the p-step).  Nothing but the state load/store at the start/end of the launch
-// touches global memory.
-#include <cooperative_groups.h>
-
+// by a thread-block cluster of CL CTAs; CTA `rank` owns a band of TR*R tile rows and
+// thread (x, y) of it owns pixel column x and the R consecutive band rows y*R ..
+// y*R+R-1 (the 32 lanes of a warp are 32 adjacent columns).  Registers hold, per
+// pixel: u, the torn dual dofs p1 (top edge) and p2 (left edge), their proximal
+// centres h1, h2 and the extrapolation pbar1.  Shared memory holds what neighbours
+// read: u (zero-padded on the left), pbar2 (the tile's right side in column mc),
+// f (or g), the first-row pbar1 of every thread row, and two halo rows that the
+// neighbouring CTAs of the cluster write through distributed shared memory (u of
+// the row above the band, pbar1 of the row below it).  The halo of the tile's top
+// row and the padding left of column 0 stay zero, so the interface formulas
+// D_s u = +u on the top and left sides need no branch; an inactive side (image
+// boundary) is kept at 0 by clamping its dofs to [-0, 0].
+//
+// Synchronisation per inner iteration: two CTA barriers and two phases of the
+// cluster barrier.  In each half-step a CTA first computes the row its neighbour
+// needs, stores it into the neighbour's halo, arrives on the cluster barrier, then
+// computes its other rows; the matching wait comes a half-step later, so the
+// cross-SM latency of the cluster barrier hides behind the interior work.  Only
+// warps that wrote to a neighbour arrive with release semantics.
 #include "internal.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace ddtv {
 
 namespace {
 
-template <int CL>
-__device__ __forceinline__ void band_sync() {
-  if constexpr (CL > 1) {
-    cg::this_cluster().sync();  // barrier.cluster.arrive.release + wait.acquire
-  } else {
-    __syncthreads();
-  }
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t map_rank(uint32_t addr, int rank) {
+  uint32_t out;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(addr), "r"(rank));
+  return out;
 }
+
+__device__ __forceinline__ void st_cluster(uint32_t addr, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+
+template <bool RELEASE>
+__device__ __forceinline__ void cluster_arrive() {
+  if (RELEASE)
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  else
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
 template <int BW, int R, int TR>
 struct SmemLayout {
   static constexpr int BAND = TR * R;
-  static constexpr int U = 0;                          // BAND x BW     u of the band
-  static constexpr int UH = U + BAND * BW;             // BW            u of the row above the band
-  static constexpr int P2 = UH + BW;                   // BAND x (BW+1) pbar2 (left edges; column mc = right side)
-  static constexpr int P1 = P2 + BAND * (BW + 1);      // (TR+1) x BW   pbar1 of each thread row's first row;
-                                                       //               row TR: first row of the band below
-  static constexpr int PR = P1 + (TR + 1) * BW;        // BAND          right-side p
-  static constexpr int HR = PR + BAND;                 // BAND          right-side phat
+  static constexpr int US = BW + 1;                    // row stride of u (index 0 = zero pad)
+  static constexpr int QS = BW + 1;                    // row stride of pbar2 (index mc = right side)
+  static constexpr int U = 0;                          // BAND x US   u of the band
+  static constexpr int UH = U + BAND * US;             // US          u of the row above the band
+  static constexpr int Q2 = UH + US;                   // BAND x QS   pbar2
+  static constexpr int Q1 = Q2 + BAND * QS;            // TR x BW     pbar1 of each thread row's first row
+  static constexpr int Q1H = Q1 + TR * BW;             // BW          pbar1 of the row below the band
+  static constexpr int F = Q1H + BW;                   // BAND x BW   f (or g)
+  static constexpr int PR = F + BAND * BW;             // BAND        right-side p
+  static constexpr int HR = PR + BAND;                 // BAND        right-side phat
   static constexpr int FLOATS = HR + BAND;
   static constexpr size_t BYTES = sizeof(float) * FLOATS;
 };
 
+// p_update with the clamp to [-lim, lim]; lim = 0 pins an inactive dof at 0
+__device__ __forceinline__ void p_update_lim(float& p, float& pbar, float du, float phat, const Coef& c, float lim) {
+  const float t = fmaf(c.pc, du, fmaf(c.pa, p, c.pb * phat));
+  const float pn = fminf(fmaxf(t, -lim), lim);
+  pbar = fmaf(c.th, pn - p, pn);
+  p = pn;
+}
+
 template <int BW, int R, int TR, int CL, int FID, bool MASK>
-__global__ void __launch_bounds__(BW* TR) k_fused(const LocalArgs A) {
+__global__ void __launch_bounds__(BW* TR, (BW * TR <= 256 ? 2 : 1)) k_fused(const LocalArgs A) {
   using L = SmemLayout<BW, R, TR>;
   constexpr int BAND = L::BAND;
   extern __shared__ float smem[];
   float* sU = smem + L::U;
   float* sUh = smem + L::UH;
-  float* sP2 = smem + L::P2;
-  float* sP1 = smem + L::P1;
+  float* sQ2 = smem + L::Q2;
+  float* sQ1 = smem + L::Q1;
+  float* sQ1h = smem + L::Q1H;
+  float* sF = smem + L::F;
   float* sPR = smem + L::PR;
   float* sHR = smem + L::HR;
 
@@ -69,34 +97,52 @@ __global__ void __launch_bounds__(BW* TR) k_fused(const LocalArgs A) {
   const int c0 = part_start(b, g.W, g.NC), mc = part_start(b + 1, g.W, g.NC) - c0;
   const bool s_top = a > 0, s_bot = a + 1 < g.NR, s_lft = b > 0, s_rgt = b + 1 < g.NC;
   const int j = threadIdx.x, ty = threadIdx.y;
-  const int lr0 = ty * R;               // first band row of this thread
-  const int i0 = rank * BAND + lr0;     // first tile row of this thread
+  const int lr0 = ty * R;            // first band row of this thread
+  const int i0 = rank * BAND + lr0;  // first tile row of this thread
   const bool col_ok = j < mc;
   const int W2 = g.W + g.NC;
   const int gj = c0 + j;
   const float tau = A.tau;
+  // clamp limits: 0 keeps an image-boundary dof at 0
+  const float lim_left = (j == 0 && !s_lft) ? 0.f : 1.f;
+  const float lim_top = (i0 == 0 && !s_top) ? 0.f : 1.f;  // applies to r = 0 only
+  const int rb = mr - 1 - i0;                              // r of the tile's last row, if in [0, R)
+  // the band's last row is read by the CTA below, its first row by the CTA above
+  const bool push_down = CL > 1 && ty == TR - 1 && rank + 1 < CL;
+  const bool push_up = CL > 1 && ty == 0 && rank > 0;
+  uint32_t remote_uh = 0, remote_q1h = 0;
+  if (CL > 1) {
+    if (push_down) remote_uh = map_rank(smem_addr(sUh + 1 + j), rank + 1);
+    if (push_up) remote_q1h = map_rank(smem_addr(sQ1h + j), rank - 1);
+  }
 
-  float u[R], p1[R], p2[R], h1[R], h2[R], q1[R], q2[R], fg[R];
+  float u[R], p1[R], p2[R], h1[R], h2[R], q1[R];
   uint32_t in_d = 0;
-  float pB = 0.f, hB = 0.f, qB = 0.f;   // bottom side of the tile (thread owning row mr-1)
+  float pB = 0.f, hB = 0.f, qB = 0.f;  // bottom side of the tile (thread row holding row mr-1)
 
   // ---- load the tile's state and build the proximal centre
+  // The tile's first row sees u = 0 above it.  The other CTAs' halos are written by
+  // their neighbours before every read; sQ1h is only read by rows that either have a
+  // neighbour below or lie outside the tile (their values are never stored).
+  if (rank == 0) {
+    if (j == 0) sUh[0] = 0.f;
+    sUh[1 + j] = 0.f;
+  }
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int i = i0 + r;
-    u[r] = p1[r] = p2[r] = h1[r] = h2[r] = fg[r] = 0.f;
+    float uv = 0.f, fv = 0.f, a1 = 0.f, a2 = 0.f, b1 = 0.f, b2 = 0.f;
     if (col_ok && i < mr) {
       const int gi = r0 + i;
       const size_t px = (size_t)gi * g.W + gj;
-      u[r] = A.u[px];
-      float fv = A.f[px];
+      uv = A.u[px];
+      fv = A.f[px];
       if (FID == FID_SEG) fv = (fv - A.c1) * (fv - A.c1) - (fv - A.c2) * (fv - A.c2);
-      fg[r] = fv;
       if (MASK && A.mask[px]) in_d |= 1u << r;
-      p1[r] = A.P1[(size_t)(gi + a) * g.W + gj];
-      p2[r] = A.P2[(size_t)gi * W2 + gj + b];
-      h1[r] = (i == 0 && s_top) ? phat_t(p1[r], A.lamh[(size_t)(a - 1) * g.W + gj], tau) : p1[r];
-      h2[r] = (j == 0 && s_lft) ? phat_t(p2[r], A.lamv[(size_t)(b - 1) * g.H + gi], tau) : p2[r];
+      a1 = A.P1[(size_t)(gi + a) * g.W + gj];
+      a2 = A.P2[(size_t)gi * W2 + gj + b];
+      b1 = (i == 0 && s_top) ? phat_t(a1, A.lamh[(size_t)(a - 1) * g.W + gj], tau) : a1;
+      b2 = (j == 0 && s_lft) ? phat_t(a2, A.lamv[(size_t)(b - 1) * g.H + gi], tau) : a2;
       if (i == mr - 1 && s_bot) {
         pB = A.P1[(size_t)(gi + a + 1) * g.W + gj];
         hB = phat_s(pB, A.lamh[(size_t)a * g.W + gj], tau);
@@ -109,74 +155,89 @@ __global__ void __launch_bounds__(BW* TR) k_fused(const LocalArgs A) {
         }
         sPR[lr0 + r] = pr;
         sHR[lr0 + r] = hr;
-        sP2[(lr0 + r) * (BW + 1) + mc] = pr;
+        sQ2[(lr0 + r) * L::QS + mc] = pr;
       }
     }
-    q1[r] = p1[r];
-    q2[r] = p2[r];
-    if (col_ok) sP2[(lr0 + r) * (BW + 1) + j] = q2[r];  // column mc belongs to the right side
+    u[r] = uv;
+    p1[r] = a1;
+    p2[r] = a2;
+    h1[r] = b1;
+    h2[r] = b2;
+    q1[r] = a1;
+    sF[(lr0 + r) * BW + j] = fv;
+    sU[(lr0 + r) * L::US] = 0.f;  // left padding (every thread writes the same value)
+    if (col_ok) sQ2[(lr0 + r) * L::QS + j] = a2;
   }
   qB = pB;
-  sP1[ty * BW + j] = q1[0];
-  if (CL > 1 && ty == 0 && rank > 0) {
-    float* up = cg::this_cluster().map_shared_rank(sP1, rank - 1);
-    up[TR * BW + j] = q1[0];
+  sQ1[ty * BW + j] = q1[0];
+  if (push_up) st_cluster(remote_q1h, q1[0]);
+  __syncthreads();
+  if (CL > 1) {
+    if (push_up) cluster_arrive<true>(); else cluster_arrive<false>();
   }
-  band_sync<CL>();
+
+  const float4* coef4 = reinterpret_cast<const float4*>(A.coef);
+
+  auto u_px = [&](int r, const Coef& c) {
+    const int lr = lr0 + r;
+    float below;
+    if (r == rb) below = qB;                                 // the tile's bottom side
+    else if (r + 1 < R) below = q1[r + 1];
+    else if (ty + 1 < TR) below = sQ1[(ty + 1) * BW + j];
+    else below = sQ1h[j];                                    // first row of the band below
+    const float left = sQ2[lr * L::QS + j];
+    const float right = sQ2[lr * L::QS + j + 1];
+    const float d = div_px(q1[r], below, left, right);
+    u[r] = u_update<FID>(u[r], d, sF[lr * BW + j], MASK && ((in_d >> r) & 1u), c);
+    sU[lr * L::US + j + 1] = u[r];
+  };
+
+  auto p_px = [&](int r, const Coef& c) {
+    const int lr = lr0 + r;
+    float above;
+    if (r > 0) above = u[r - 1];
+    else if (ty > 0) above = sU[(lr - 1) * L::US + j + 1];
+    else above = sUh[j + 1];                                 // 0 above the tile's first row
+    p_update_lim(p1[r], q1[r], u[r] - above, h1[r], c, r == 0 ? lim_top : 1.f);
+    float q2;
+    p_update_lim(p2[r], q2, u[r] - sU[lr * L::US + j], h2[r], c, lim_left);
+    if (r == rb && s_bot) p_update(pB, qB, -u[r], hB, c);
+    if (j == mc - 1 && s_rgt) {
+      float pr = sPR[lr], qr;
+      p_update(pr, qr, -u[r], sHR[lr], c);
+      sPR[lr] = pr;
+      sQ2[lr * L::QS + mc] = qr;
+    }
+    if (col_ok) sQ2[lr * L::QS + j] = q2;
+  };
 
   // ---- inner iterations
   for (int k = 0; k < A.K; ++k) {
-    const Coef c = A.coef[k];
-    // u-step: u <- prox(u + sigma_k div_s pbar)
+    const float4 ca = __ldg(coef4 + 2 * k), cb = __ldg(coef4 + 2 * k + 1);
+    const Coef c{ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+    // u-step: the band's last row first (the CTA below needs it)
+    if (CL > 1) cluster_wait();
+    u_px(R - 1, c);
+    if (push_down) st_cluster(remote_uh, u[R - 1]);
+    if (CL > 1) {
+      if (push_down) cluster_arrive<true>(); else cluster_arrive<false>();
+    }
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int i = i0 + r;
-      if (col_ok && i < mr) {
-        const float below = (i == mr - 1) ? qB : (r + 1 < R ? q1[r + 1] : sP1[(ty + 1) * BW + j]);
-        const float right = sP2[(lr0 + r) * (BW + 1) + j + 1];
-        const float d = div_px(q1[r], below, q2[r], right);
-        u[r] = u_update<FID>(u[r], d, fg[r], MASK && ((in_d >> r) & 1u), c);
-      }
-      sU[(lr0 + r) * BW + j] = u[r];
+    for (int r = 0; r + 1 < R; ++r) u_px(r, c);
+    __syncthreads();
+    // p-step: the band's first row first (the CTA above needs its pbar1)
+    if (CL > 1) cluster_wait();
+    p_px(0, c);
+    sQ1[ty * BW + j] = q1[0];
+    if (push_up) st_cluster(remote_q1h, q1[0]);
+    if (CL > 1) {
+      if (push_up) cluster_arrive<true>(); else cluster_arrive<false>();
     }
-    if (CL > 1 && ty == TR - 1 && rank + 1 < CL) {
-      float* dn = cg::this_cluster().map_shared_rank(sUh, rank + 1);
-      dn[j] = u[R - 1];
-    }
-    band_sync<CL>();
-    // p-step on every active dof owned by this thread
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int i = i0 + r;
-      if (col_ok && i < mr) {
-        if (i > 0) {
-          const float above = r > 0 ? u[r - 1] : (ty > 0 ? sU[(lr0 - 1) * BW + j] : sUh[j]);
-          p_update(p1[r], q1[r], u[r] - above, h1[r], c);
-        } else if (s_top) {
-          p_update(p1[r], q1[r], u[r], h1[r], c);
-        }
-        if (j > 0) {
-          p_update(p2[r], q2[r], u[r] - sU[(lr0 + r) * BW + j - 1], h2[r], c);
-        } else if (s_lft) {
-          p_update(p2[r], q2[r], u[r], h2[r], c);
-        }
-        if (i == mr - 1 && s_bot) p_update(pB, qB, -u[r], hB, c);
-        if (j == mc - 1 && s_rgt) {
-          float pr = sPR[lr0 + r], qr;
-          p_update(pr, qr, -u[r], sHR[lr0 + r], c);
-          sPR[lr0 + r] = pr;
-          sP2[(lr0 + r) * (BW + 1) + mc] = qr;
-        }
-      }
-      if (col_ok) sP2[(lr0 + r) * (BW + 1) + j] = q2[r];
-    }
-    sP1[ty * BW + j] = q1[0];
-    if (CL > 1 && ty == 0 && rank > 0) {
-      float* up = cg::this_cluster().map_shared_rank(sP1, rank - 1);
-      up[TR * BW + j] = q1[0];
-    }
-    band_sync<CL>();
+    for (int r = 1; r < R; ++r) p_px(r, c);
+    __syncthreads();
   }
+  if (CL > 1) cluster_wait();  // no CTA leaves while a neighbour may still write its halo
 
   // ---- store u^{n+1}, p~^{n+1} and the interface strips
 #pragma unroll
@@ -202,25 +263,231 @@ __global__ void __launch_bounds__(BW* TR) k_fused(const LocalArgs A) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Full-tile kernel: every subdomain is exactly 128 x 128 (the partition of the
+// benchmark workloads).  Same arithmetic as k_fused, without any per-pixel
+// boundary test: the band's halo rows live in the shared arrays (row 0 of sU is
+// the row above the band, row TR of sQ1 the row below it), the tile's bottom side
+// is the "row below" of the last CTA, and the right side's dofs are updated by
+// lanes 0..R-1 of each thread row's first warp (one dof per lane).
+template <int R, int TR>
+struct FullLayout {
+  static constexpr int BW = 128;
+  static constexpr int BAND = TR * R;
+  static constexpr int US = BW + 1;                    // u row stride; index 0 = zero pad
+  static constexpr int QS = BW + 1;                    // pbar2 row stride; index 128 = right side
+  static constexpr int U = 0;                          // (BAND + 1) x US: row 0 = row above the band
+  static constexpr int Q2 = U + (BAND + 1) * US;       // BAND x QS
+  static constexpr int Q1 = Q2 + BAND * QS;            // (TR + 1) x BW: first-row pbar1 per thread row; row TR = below
+  static constexpr int F = Q1 + (TR + 1) * BW;         // BAND x BW
+  static constexpr int PR = F + BAND * BW;             // BAND right-side p
+  static constexpr int HR = PR + BAND;                 // BAND right-side phat
+  static constexpr int CO = (HR + BAND + 3) & ~3;      // kMaxSmemCoef x 8 coefficients (16-byte aligned)
+  static constexpr int FLOATS = CO + 8 * 64;
+  static constexpr size_t BYTES = sizeof(float) * FLOATS;
+  static constexpr int kMaxSmemCoef = 64;
+};
+
+template <int R, int TR, int CL, int MINB, int FID, bool MASK>
+__global__ void __launch_bounds__(128 * TR, MINB) k_fused_full(const LocalArgs A) {
+  using L = FullLayout<R, TR>;
+  constexpr int BW = L::BW, BAND = L::BAND;
+  static_assert(CL * BAND == 128, "a cluster covers the 128 rows of a tile");
+  extern __shared__ float smem[];
+  float* sU = smem + L::U;
+  float* sQ2 = smem + L::Q2;
+  float* sQ1 = smem + L::Q1;
+  float* sF = smem + L::F;
+  float* sPR = smem + L::PR;
+  float* sHR = smem + L::HR;
+  float* sCo = smem + L::CO;
+
+  const Grid g = A.g;
+  const int rank = CL > 1 ? (int)blockIdx.x : 0;
+  const int b = blockIdx.y, a = blockIdx.z;
+  const int r0 = a * 128, c0 = b * 128;
+  const bool s_top = a > 0, s_bot = a + 1 < g.NR, s_lft = b > 0, s_rgt = b + 1 < g.NC;
+  const int j = threadIdx.x, ty = threadIdx.y;
+  const int lr0 = ty * R;
+  const int i0 = rank * BAND + lr0;
+  const int W2 = g.W + g.NC;
+  const int gj = c0 + j;
+  const float tau = A.tau;
+  const float lim_left = (j == 0 && !s_lft) ? 0.f : 1.f;
+  const float lim_top = (i0 == 0 && !s_top) ? 0.f : 1.f;
+  const bool last_row_here = rank == CL - 1 && ty == TR - 1;  // holds the tile's bottom row
+  const bool push_down = CL > 1 && ty == TR - 1 && rank + 1 < CL;
+  const bool push_up = CL > 1 && ty == 0 && rank > 0;
+  // right side: lane l < R of warp 0 of each thread row owns the dof of band row lr0 + l
+  const bool right_lane = s_rgt && j < R;
+  uint32_t remote_u = 0, remote_q1 = 0;
+  if (push_down) remote_u = map_rank(smem_addr(sU + 1 + j), rank + 1);           // row 0 (above) of rank + 1
+  if (push_up) remote_q1 = map_rank(smem_addr(sQ1 + TR * BW + j), rank - 1);      // row TR (below) of rank - 1
+
+  float u[R], p1[R], p2[R], h1[R], h2[R], q1[R];
+  uint32_t in_d = 0;
+  float pB = 0.f, hB = 0.f;
+
+  for (int q = threadIdx.x + threadIdx.y * BW; q < 8 * min(A.K, L::kMaxSmemCoef); q += BW * TR)
+    sCo[q] = reinterpret_cast<const float*>(A.coef)[q];
+  if (rank == 0) sU[1 + j] = 0.f;  // u = 0 above the tile's first row
+  if (j == 0) sU[0] = 0.f;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int gi = r0 + i0 + r;
+    const size_t px = (size_t)gi * g.W + gj;
+    u[r] = A.u[px];
+    float fv = A.f[px];
+    if (FID == FID_SEG) fv = (fv - A.c1) * (fv - A.c1) - (fv - A.c2) * (fv - A.c2);
+    sF[(lr0 + r) * BW + j] = fv;
+    if (MASK && A.mask[px]) in_d |= 1u << r;
+    p1[r] = A.P1[(size_t)(gi + a) * g.W + gj];
+    p2[r] = A.P2[(size_t)gi * W2 + gj + b];
+    h1[r] = p1[r];
+    h2[r] = p2[r];
+    q1[r] = p1[r];
+    sQ2[(lr0 + r) * L::QS + j] = p2[r];
+    sU[(lr0 + r + 1) * L::US] = 0.f;
+  }
+  if (i0 == 0 && s_top) h1[0] = phat_t(p1[0], A.lamh[(size_t)(a - 1) * g.W + gj], tau);
+  if (j == 0 && s_lft) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) h2[r] = phat_t(p2[r], A.lamv[(size_t)(b - 1) * g.H + r0 + i0 + r], tau);
+  }
+  if (last_row_here) {
+    if (s_bot) {
+      pB = A.P1[(size_t)(r0 + 128 + a) * g.W + gj];
+      hB = phat_s(pB, A.lamh[(size_t)a * g.W + gj], tau);
+    }
+    sQ1[TR * BW + j] = pB;
+  }
+  if (j < R) {  // right side of band row lr0 + j
+    float pr = 0.f, hr = 0.f;
+    if (s_rgt) {
+      const int gi = r0 + i0 + j;
+      pr = A.P2[(size_t)gi * W2 + c0 + 128 + b];
+      hr = phat_s(pr, A.lamv[(size_t)b * g.H + gi], tau);
+    }
+    sPR[lr0 + j] = pr;
+    sHR[lr0 + j] = hr;
+    sQ2[(lr0 + j) * L::QS + 128] = pr;
+  }
+  sQ1[ty * BW + j] = q1[0];
+  if (push_up) st_cluster(remote_q1, q1[0]);
+  __syncthreads();
+  if (CL > 1) {
+    if (push_up) cluster_arrive<true>(); else cluster_arrive<false>();
+  }
+
+  float* sUr = sU + (lr0 + 1) * L::US + j + 1;  // u of band row lr0 + r, column j at sUr[r * US]
+  float* sQ2r = sQ2 + lr0 * L::QS + j;
+  const float* sFr = sF + lr0 * BW + j;
+
+  for (int k = 0; k < A.K; ++k) {
+    Coef c;
+    if (k < L::kMaxSmemCoef) {
+      const float4 ca = *reinterpret_cast<const float4*>(sCo + 8 * k);
+      const float4 cb = *reinterpret_cast<const float4*>(sCo + 8 * k + 4);
+      c = Coef{ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+    } else {
+      c = A.coef[k];
+    }
+    // ---- u-step; the band's last row first
+    if (CL > 1) cluster_wait();
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+      const int r = (rr + R - 1) % R;  // R-1, 0, 1, ..., R-2
+      const float below = r + 1 < R ? q1[r + 1] : sQ1[(ty + 1) * BW + j];
+      const float d = div_px(q1[r], below, sQ2r[r * L::QS], sQ2r[r * L::QS + 1]);
+      u[r] = u_update<FID>(u[r], d, sFr[r * BW], MASK && ((in_d >> r) & 1u), c);
+      sUr[r * L::US] = u[r];
+      if (rr == 0) {
+        if (push_down) st_cluster(remote_u, u[R - 1]);
+        if (CL > 1) {
+          if (push_down) cluster_arrive<true>(); else cluster_arrive<false>();
+        }
+      }
+    }
+    __syncthreads();
+    // ---- p-step; the band's first row first
+    if (CL > 1) cluster_wait();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float above = r > 0 ? u[r - 1] : sUr[-L::US];
+      p_update_lim(p1[r], q1[r], u[r] - above, h1[r], c, r == 0 ? lim_top : 1.f);
+      float q2;
+      p_update_lim(p2[r], q2, u[r] - sUr[r * L::US - 1], h2[r], c, lim_left);
+      sQ2r[r * L::QS] = q2;
+      if (r == 0) {
+        sQ1[ty * BW + j] = q1[0];
+        if (push_up) st_cluster(remote_q1, q1[0]);
+        if (CL > 1) {
+          if (push_up) cluster_arrive<true>(); else cluster_arrive<false>();
+        }
+      }
+    }
+    if (last_row_here && s_bot) {  // the tile's bottom side: D_s u = -u
+      float qB;
+      p_update(pB, qB, -u[R - 1], hB, c);
+      sQ1[TR * BW + j] = qB;
+    }
+    if (right_lane) {  // the tile's right side of band row lr0 + j: D_s u = -u
+      const int lr = lr0 + j;
+      float pr = sPR[lr], qr;
+      p_update(pr, qr, -sU[(lr + 1) * L::US + 128], sHR[lr], c);
+      sPR[lr] = pr;
+      sQ2[lr * L::QS + 128] = qr;
+    }
+    __syncthreads();
+  }
+  if (CL > 1) cluster_wait();
+
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int gi = r0 + i0 + r;
+    A.u[(size_t)gi * g.W + gj] = u[r];
+    A.P1[(size_t)(gi + a) * g.W + gj] = p1[r];
+    A.P2[(size_t)gi * W2 + gj + b] = p2[r];
+  }
+  if (i0 == 0 && s_top) A.out.ST[(size_t)(a - 1) * g.W + gj] = p1[0];
+  if (j == 0 && s_lft) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) A.out.SL[(size_t)(b - 1) * g.H + r0 + i0 + r] = p2[r];
+  }
+  if (last_row_here && s_bot) {
+    A.P1[(size_t)(r0 + 128 + a) * g.W + gj] = pB;
+    A.out.SB[(size_t)a * g.W + gj] = pB;
+  }
+  if (right_lane) {
+    const int gi = r0 + i0 + j;
+    const float pr = sPR[lr0 + j];
+    A.P2[(size_t)gi * W2 + c0 + 128 + b] = pr;
+    A.out.SR[(size_t)b * g.H + gi] = pr;
+  }
+}
+
 struct Config {
   int BW, R, TR, CL;
   const char* name;
 };
 
-// Configurations, smallest first; the first whose tile fits is used.
+// Hardware mappings.  Class 0: tiles up to 32 x 32; class 1: up to 64 x 64; class 2:
+// up to 128 x 128, where `variant` picks among the mappings (0 is the default).
 constexpr Config kConfigs[] = {
-    {32, 8, 4, 1, "bw32_r8_tr4_cl1"},      // tiles up to 32 x 32
-    {64, 8, 4, 2, "bw64_r8_tr4_cl2"},      // up to 64 x 64
-    {128, 8, 2, 8, "bw128_r8_tr2_cl8"},    // up to 128 x 128
+    {32, 8, 4, 1, "bw32_r8_tr4_cl1"},      // class 0
+    {64, 8, 8, 1, "bw64_r8_tr8_cl1"},      // class 1
+    {128, 8, 2, 8, "bw128_r8_tr2_cl8"},    // class 2, variant 0: 256 threads, 2 CTAs/SM
+    {128, 8, 4, 4, "bw128_r8_tr4_cl4"},    // class 2, variant 1: 512 threads, 1 CTA/SM
+    {128, 16, 2, 4, "bw128_r16_tr2_cl4"},  // class 2, variant 2: 256 threads, 16 rows/thread
 };
+constexpr int kNumConfigs = (int)(sizeof(kConfigs) / sizeof(kConfigs[0]));
+constexpr int kNumVariants = 3;
 
 template <int BW, int R, int TR, int CL, int FID, bool MASK>
 cudaError_t launch_one(const LocalArgs& a, cudaStream_t st) {
   using L = SmemLayout<BW, R, TR>;
-  auto kern = k_fused<BW, R, TR, CL, FID, MASK>;
-  // every configuration stays under the 48 KB of dynamic shared memory available
-  // without an opt-in attribute, so nothing host-side is needed during graph capture
-  static_assert(L::BYTES <= 48 * 1024, "fused configuration needs an opt-in shared-memory attribute");
+  // configurations above 48 KB of shared memory need the opt-in attribute, set by
+  // fused_prepare() when the handle is created (never during graph capture)
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CL, a.g.NC, a.g.NR);
   cfg.blockDim = dim3(BW, TR, 1);
@@ -233,7 +500,7 @@ cudaError_t launch_one(const LocalArgs& a, cudaStream_t st) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, a);
+  return cudaLaunchKernelEx(&cfg, k_fused<BW, R, TR, CL, FID, MASK>, a);
 }
 
 template <int BW, int R, int TR, int CL>
@@ -246,34 +513,119 @@ cudaError_t launch_fid(const LocalArgs& a, int fid, cudaStream_t st) {
   }
 }
 
-int pick(int mr, int mc) {
-  for (int q = 0; q < (int)(sizeof(kConfigs) / sizeof(kConfigs[0])); ++q) {
-    const Config& c = kConfigs[q];
-    if (mc <= c.BW && mr <= c.R * c.TR * c.CL) return q;
+template <int R, int TR, int CL, int MINB, int FID, bool MASK>
+cudaError_t launch_full_one(const LocalArgs& a, cudaStream_t st) {
+  using L = FullLayout<R, TR>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL, a.g.NC, a.g.NR);
+  cfg.blockDim = dim3(128, TR, 1);
+  cfg.dynamicSmemBytes = L::BYTES;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_fused_full<R, TR, CL, MINB, FID, MASK>, a);
+}
+
+template <int R, int TR, int CL, int MINB>
+cudaError_t launch_full(const LocalArgs& a, int fid, cudaStream_t st) {
+  const bool m = a.mask != nullptr;
+  switch (fid) {
+    case FID_L2: return m ? launch_full_one<R, TR, CL, MINB, FID_L2, true>(a, st) : launch_full_one<R, TR, CL, MINB, FID_L2, false>(a, st);
+    case FID_L1: return m ? launch_full_one<R, TR, CL, MINB, FID_L1, true>(a, st) : launch_full_one<R, TR, CL, MINB, FID_L1, false>(a, st);
+    default: return launch_full_one<R, TR, CL, MINB, FID_SEG, false>(a, st);
   }
+}
+
+template <int R, int TR, int CL, int MINB, int FID, bool MASK>
+cudaError_t prepare_full_one() {
+  using L = FullLayout<R, TR>;
+  return cudaFuncSetAttribute(k_fused_full<R, TR, CL, MINB, FID, MASK>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+}
+
+template <int R, int TR, int CL, int MINB>
+cudaError_t prepare_full() {
+  cudaError_t e;
+  if ((e = prepare_full_one<R, TR, CL, MINB, FID_L2, false>()) != cudaSuccess) return e;
+  if ((e = prepare_full_one<R, TR, CL, MINB, FID_L2, true>()) != cudaSuccess) return e;
+  if ((e = prepare_full_one<R, TR, CL, MINB, FID_L1, false>()) != cudaSuccess) return e;
+  if ((e = prepare_full_one<R, TR, CL, MINB, FID_L1, true>()) != cudaSuccess) return e;
+  return prepare_full_one<R, TR, CL, MINB, FID_SEG, false>();
+}
+
+template <int BW, int R, int TR, int CL, int FID, bool MASK>
+cudaError_t prepare_one() {
+  using L = SmemLayout<BW, R, TR>;
+  return cudaFuncSetAttribute(k_fused<BW, R, TR, CL, FID, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)L::BYTES);
+}
+
+template <int BW, int R, int TR, int CL>
+cudaError_t prepare_fid() {
+  cudaError_t e;
+  if ((e = prepare_one<BW, R, TR, CL, FID_L2, false>()) != cudaSuccess) return e;
+  if ((e = prepare_one<BW, R, TR, CL, FID_L2, true>()) != cudaSuccess) return e;
+  if ((e = prepare_one<BW, R, TR, CL, FID_L1, false>()) != cudaSuccess) return e;
+  if ((e = prepare_one<BW, R, TR, CL, FID_L1, true>()) != cudaSuccess) return e;
+  return prepare_one<BW, R, TR, CL, FID_SEG, false>();
+}
+
+// index into kConfigs for a tile shape and variant, -1 if none fits
+int pick(int mr, int mc, int variant) {
+  if (mc <= 32 && mr <= 32) return 0;
+  if (mc <= 64 && mr <= 64) return 1;
+  if (mc <= 128 && mr <= 128 && variant >= 0 && variant < kNumVariants) return 2 + variant;
   return -1;
 }
 
 }  // namespace
 
 void fused_max_tile(int* rows, int* cols) {
-  const Config& c = kConfigs[sizeof(kConfigs) / sizeof(kConfigs[0]) - 1];
-  *rows = c.R * c.TR * c.CL;
-  *cols = c.BW;
+  *rows = 128;
+  *cols = 128;
 }
 
-const char* fused_config_name(int mr, int mc) {
-  const int q = pick(mr, mc);
+int fused_num_variants() { return kNumVariants; }
+
+const char* fused_config_name(int mr, int mc, int variant) {
+  const int q = pick(mr, mc, variant);
   return q < 0 ? "none" : kConfigs[q].name;
 }
 
-cudaError_t launch_fused_local(const LocalArgs& a, int fid, cudaStream_t st) {
+cudaError_t fused_prepare() {
+  cudaError_t e;
+  if ((e = prepare_fid<32, 8, 4, 1>()) != cudaSuccess) return e;
+  if ((e = prepare_fid<64, 8, 8, 1>()) != cudaSuccess) return e;
+  if ((e = prepare_fid<128, 8, 2, 8>()) != cudaSuccess) return e;
+  if ((e = prepare_fid<128, 8, 4, 4>()) != cudaSuccess) return e;
+  if ((e = prepare_fid<128, 16, 2, 4>()) != cudaSuccess) return e;
+  if ((e = prepare_full<8, 2, 8, 2>()) != cudaSuccess) return e;
+  if ((e = prepare_full<8, 4, 4, 1>()) != cudaSuccess) return e;
+  return prepare_full<8, 2, 8, 3>();
+}
+
+cudaError_t launch_fused_local(const LocalArgs& a, int fid, int variant, cudaStream_t st) {
   // largest tile of the (ragged) partition
   const int mr = (a.g.H + a.g.NR - 1) / a.g.NR, mc = (a.g.W + a.g.NC - 1) / a.g.NC;
-  switch (pick(mr, mc)) {
+  if (a.g.H == 128 * a.g.NR && a.g.W == 128 * a.g.NC) {  // every tile exactly 128 x 128
+    switch (variant) {
+      case 0: return launch_full<8, 2, 8, 2>(a, fid, st);  // 256 threads, 2 CTAs/SM
+      case 1: return launch_full<8, 4, 4, 1>(a, fid, st);  // 512 threads, 1 CTA/SM
+      case 2: return launch_full<8, 2, 8, 3>(a, fid, st);  // 256 threads, 3 CTAs/SM (<= 85 registers)
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (pick(mr, mc, variant)) {
     case 0: return launch_fid<32, 8, 4, 1>(a, fid, st);
-    case 1: return launch_fid<64, 8, 4, 2>(a, fid, st);
+    case 1: return launch_fid<64, 8, 8, 1>(a, fid, st);
     case 2: return launch_fid<128, 8, 2, 8>(a, fid, st);
+    case 3: return launch_fid<128, 8, 4, 4>(a, fid, st);
+    case 4: return launch_fid<128, 16, 2, 4>(a, fid, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -129,17 +129,17 @@ def test_energy_and_gap_kernels():
     u = (f + 0.01 * rng.standard_normal(f.shape)).astype(np.float32)
     mask = (rng.uniform(size=f.shape) < 0.2).astype(np.uint8)
     for fid, m in (("l2", None), ("l2", mask), ("l1", mask), ("seg", None)):
-        p = L.make_params(257, 131, 2, 2, fidelity=fid, alpha=7.0, c1=0.2, c2=0.8)
+        p = L.make_params(257, 131, 3, 2, fidelity=fid, alpha=7.0, c1=0.2, c2=0.8)
         s = L.Solver(p)
         ud = torch.from_numpy(np.clip(u, 0, 1) if fid == "seg" else u).cuda()
         J = s.energy(ud, torch.from_numpy(f).cuda(), None if m is None else torch.from_numpy(m).cuda())
-        pr = oracle.Problem(257, 131, 2, 2, fidelity=fid, alpha=7.0, c1=0.2, c2=0.8)
+        pr = oracle.Problem(257, 131, 3, 2, fidelity=fid, alpha=7.0, c1=0.2, c2=0.8)
         Jo = oracle.energy(pr, ud.cpu().numpy().astype(np.float64), f.astype(np.float64), m)
         assert abs(J - Jo) <= 1e-6 * abs(Jo), (fid, J, Jo)
     # duality gap of a DD iterate: same J and dual value as the oracle on the same state
-    s, g, _, _ = _run_gpu(f, None, 40, sub_rows=2, sub_cols=3, fidelity="l2", alpha=7.0)
+    s, g, _, _ = _run_gpu(f, None, 40, sub_rows=3, sub_cols=3, fidelity="l2", alpha=7.0)
     J, D = s.gap()
-    pr = oracle.Problem(257, 131, 2, 3, alpha=7.0)
+    pr = oracle.Problem(257, 131, 3, 3, alpha=7.0)
     p1, p2 = oracle.torn_to_global(pr, g["P1"], g["P2"])
     Do = oracle.dual_value(pr, p1, p2, f.astype(np.float64))
     Jo = oracle.energy(pr, g["u"], f.astype(np.float64))
@@ -217,3 +217,17 @@ def test_full_size_4096_sampled_parity():
     _, o = _run_oracle(f, None, 2, **kw)
     assert np.abs(g["u"] - o.u).max() <= U_TOL
     assert np.abs(g["lamh"] - o.lamh).max() <= 1e-3
+
+
+@pytest.mark.parametrize("H,W,NR,NC", [(384, 384, 3, 3), (250, 260, 2, 3), (128, 128, 1, 1)])
+def test_fused_variants_bitwise_identical(H, W, NR, NC):
+    """Every hardware mapping of a 128x128-class subdomain runs the same arithmetic."""
+    L = _gpu()
+    f, _ = synth.rof_image(H, W, 12, 0.1, 12)
+    outs = []
+    for v in range(3):
+        _, g, _, _ = _run_gpu(f, None, 7, sub_rows=NR, sub_cols=NC, alpha=8.0, variant=v)
+        outs.append(g)
+    for g in outs[1:]:
+        for k in ("u", "P1", "P2", "lamh", "lamv"):
+            assert np.array_equal(g[k], outs[0][k]), k
