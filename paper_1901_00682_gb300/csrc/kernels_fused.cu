@@ -614,8 +614,8 @@ cudaError_t launch_fused_local(const LocalArgs& a, int fid, int variant, cudaStr
   const int mr = (a.g.H + a.g.NR - 1) / a.g.NR, mc = (a.g.W + a.g.NC - 1) / a.g.NC;
   if (a.g.H == 128 * a.g.NR && a.g.W == 128 * a.g.NC) {  // every tile exactly 128 x 128
     switch (variant) {
-      case 0: return launch_full<8, 2, 8, 2>(a, fid, st);  // 256 threads, 2 CTAs/SM
-      case 1: return launch_full<8, 4, 4, 1>(a, fid, st);  // 512 threads, 1 CTA/SM
+      case 0: return launch_full<8, 4, 4, 1>(a, fid, st);  // 512 threads, 1 CTA/SM
+      case 1: return launch_full<8, 2, 8, 2>(a, fid, st);  // 256 threads, 2 CTAs/SM
       case 2: return launch_full<8, 2, 8, 3>(a, fid, st);  // 256 threads, 3 CTAs/SM (<= 85 registers)
       default: return cudaErrorInvalidValue;
     }
