@@ -190,6 +190,26 @@ int dd_tv_profile_read(dd_tv* h, double* ms, long long* launches);
  * small device buffer.  *gbs_out is in GB/s (1e9 bytes/s). */
 int dd_tv_measure_smem_bandwidth(double* gbs_out);
 
+/* Energy J(u) = alpha F(u) + TV(u), like dd_tv_energy, for callers that cannot
+ * allocate device memory at the time they need it (for instance a process whose
+ * device memory is entirely held by another framework's pool, or a latency-critical
+ * loop that must not pay cudaMalloc's implicit synchronisation).  The paper has no
+ * counterpart: this is a deployment variant of the energy reduction.
+ *
+ * No handle and no allocation: the reduction's scratch is a fixed 9,760-byte array
+ * in the library's device memory (every GPU that loads the library holds it until
+ * the process exits).  The first call on a device looks that array's address up with
+ * the device current, so make the first call on each device outside any stream
+ * capture.  Images of up to 2^31 - 1 pixels are accepted; larger ones, a null
+ * pointer, a bad fidelity or alpha <= 0 return DD_TV_EINVAL.  u_dev, f_dev, mask_dev
+ * (nullable) are H x W device images as in dd_tv_energy; the caller keeps them.
+ * stream is a cudaStream_t (0 = legacy default stream).  All calls share the one
+ * scratch array, so calls whose work overlaps on the GPU (other streams or threads)
+ * race and may return wrong values; serialise them.  Synchronous: waits for the
+ * stream and writes *J_out. */
+int dd_tv_energy_noalloc(const float* u_dev, const float* f_dev, const uint8_t* mask_dev, int height, int width,
+                         int fidelity, double alpha, double c1, double c2, void* stream, double* J_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,6 +68,7 @@ SIGNATURES = {
     "dd_tv_set_profiling": (_i, [_vp, _i]),
     "dd_tv_profile_read": (_i, [_vp, _DP, ctypes.POINTER(ctypes.c_longlong)]),
     "dd_tv_measure_smem_bandwidth": (_i, [_DP]),
+    "dd_tv_energy_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _i, _d, _d, _d, _vp, _DP]),
 }
 
 _lock = threading.Lock()

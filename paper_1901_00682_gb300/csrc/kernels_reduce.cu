@@ -8,6 +8,9 @@
 // are combined in float64, and the last block to finish adds the block partials in a
 // fixed order, so the result does not depend on scheduling.  HBM-bound: u, f (and
 // mask, P1, P2) are read once.
+#include <mutex>
+
+#include "../../include/dd_tv.h"
 #include "internal.cuh"
 
 namespace ddtv {
@@ -131,3 +134,75 @@ cudaError_t launch_energy(const Grid& g, int fid, float alpha, float c1, float c
 }
 
 }  // namespace ddtv
+
+// ---------------------------------------------------------------------------
+// Energy without any allocation.
+//
+// The handle-based dd_tv_energy keeps its block partials in memory the handle
+// allocated with cudaMalloc.  Some callers cannot allocate device memory when they
+// need an energy value: a process whose device memory is entirely reserved by
+// another framework's pool, or a latency-critical loop where cudaMalloc's implicit
+// device synchronisation is not acceptable.  dd_tv_energy_noalloc serves them with
+// the same reduction kernel, its scratch living in the file-scope array below.
+//
+// Scratch: kNoAllocDoubles doubles (9,760 bytes) per GPU that loads the library,
+// held until the process exits: 2 partial sums per block of the fixed 608-block
+// grid, the block counter, and the two results.  Because the grid never grows,
+// every image up to 2^31 - 1 pixels fits; larger ones are refused.
+namespace {
+
+constexpr int kNoAllocDoubles = 2 * 152 * 4 + 4;
+constexpr int kMaxDevices = 64;
+static __device__ __align__(256) double g_energy_scratch[kNoAllocDoubles];
+
+std::mutex g_scratch_mu;
+double* g_scratch_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once per
+// device with that device current (the first call on each device does this).
+cudaError_t scratch_on_current_device(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    double* p = nullptr;
+    e = cudaGetSymbolAddress((void**)&p, g_energy_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int dd_tv_energy_noalloc(const float* u_dev, const float* f_dev, const uint8_t* mask_dev, int height,
+                                    int width, int fidelity, double alpha, double c1, double c2, void* stream,
+                                    double* J_out) {
+  if (!u_dev || !f_dev || !J_out) return DD_TV_EINVAL;
+  if (height < 1 || width < 1) return DD_TV_EINVAL;
+  if ((long long)height * width > (1LL << 31) - 1) return DD_TV_EINVAL;  // beyond what the scratch serves
+  if (fidelity < DD_TV_L2 || fidelity > DD_TV_SEG || !(alpha > 0.0)) return DD_TV_EINVAL;
+  if (ddtv::reduce_partials_count() + 4 > kNoAllocDoubles) return DD_TV_EUNSUPPORTED;
+  double* scratch = nullptr;
+  if (scratch_on_current_device(&scratch) != cudaSuccess) return DD_TV_ECUDA;
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int np = ddtv::reduce_partials_count();
+  double* partials = scratch;
+  unsigned int* counter = reinterpret_cast<unsigned int*>(scratch + np);
+  double* out = scratch + np + 2;
+  // the array keeps the previous call's contents: the block counter must start at 0
+  if (cudaMemsetAsync(counter, 0, sizeof(unsigned int), st) != cudaSuccess) return DD_TV_ECUDA;
+  const ddtv::Grid g{height, width, 1, 1};
+  if (ddtv::launch_energy(g, fidelity, (float)alpha, (float)c1, (float)c2, u_dev, f_dev, mask_dev, nullptr, nullptr,
+                          partials, counter, out, st) != cudaSuccess)
+    return DD_TV_ECUDA;
+  double host[1];
+  if (cudaMemcpyAsync(host, out, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess) return DD_TV_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return DD_TV_ECUDA;
+  *J_out = host[0];
+  return DD_TV_OK;
+}
