@@ -176,6 +176,7 @@ LocalArgs local_args(dd_tv* h, int write_set) {
   a.lamv = h->lamv;
   a.out = h->strips[write_set];
   a.coef = h->coef;
+  a.err = h->flag;
   return a;
 }
 
@@ -303,6 +304,18 @@ int reset_state(dd_tv* h) {
   return DD_TV_OK;
 }
 
+// Reads (and clears) the device flag a kernel sets when a bounded wait ran out.
+int check_timeout(dd_tv* h) {
+  int v = 0;
+  CK(cudaMemcpyAsync(&v, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (v) {
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+    return fail(h, DD_TV_ETIMEOUT, "a device-side wait of the fused kernel ran out (results are invalid)");
+  }
+  return DD_TV_OK;
+}
+
 int energy_of(dd_tv* h, const float* u, const float* f, const uint8_t* mask, bool dual, double* out2) {
   {
     PhaseMark m(h, 2, 1);
@@ -344,7 +357,10 @@ int solve_loaded(dd_tv* h, dd_tv_stats* stats, bool sync_needed) {
     }
   }
   CK(cudaEventRecord(h->ev1, h->stream));
-  if (stats || sync_needed) CK(cudaEventSynchronize(h->ev1));
+  if (stats || sync_needed) {
+    CK(cudaEventSynchronize(h->ev1));
+    if ((rc = check_timeout(h))) return rc;
+  }
   CK(cudaGetLastError());
   if (stats) {
     float ms = 0.f;
@@ -478,6 +494,7 @@ int dd_tv_create(dd_tv** out, const dd_tv_params* p) {
   cudaError_t e;
   if ((e = cudaMemcpy(h->coef, sched.data(), sched.size() * sizeof(Coef), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemset(h->counter, 0, sizeof(unsigned int))) != cudaSuccess ||
+      (e = cudaMemset(h->flag, 0, sizeof(int))) != cudaSuccess ||
       (e = cudaEventCreate(&h->ev0)) != cudaSuccess || (e = cudaEventCreate(&h->ev1)) != cudaSuccess ||
       (e = cudaStreamCreate(&h->own)) != cudaSuccess) {
     std::snprintf(g_create_err, sizeof(g_create_err), "dd_tv_create: %s", cudaGetErrorString(e));
@@ -652,6 +669,8 @@ int dd_tv_set_profiling(dd_tv* h, int on) {
 int dd_tv_profile_read(dd_tv* h, double* ms, long long* launches) {
   if (!h) return DD_TV_EINVAL;
   CK(cudaStreamSynchronize(h->stream));
+  int rc = check_timeout(h);
+  if (rc) return rc;
   double acc[3] = {0.0, 0.0, 0.0};
   for (auto& m : h->marks) {
     float t = 0.f;

@@ -38,6 +38,7 @@ struct LocalArgs {
   const float* lamv;     // (NC-1) x H
   Strips out;            // strips of p~^{n+1} (written at the end)
   const Coef* coef;      // K coefficient sets (device)
+  int* err;              // set non-zero by a kernel whose bounded wait ran out
 };
 
 // ---- kernels_interface.cu

@@ -466,6 +466,530 @@ __global__ void __launch_bounds__(128 * TR, MINB) k_fused_full(const LocalArgs A
   }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-row kernel for exact 128 x 128 subdomains.  Warp w of a CTA owns R full rows
+// of the tile (lane l holds columns 4l .. 4l+3 of each), so horizontal neighbours
+// are in the lane's registers or one shuffle away, and the only data another warp
+// needs are a warp's first-row pbar1 (read by the warp above) and last-row u (read
+// by the warp below).  Those rows go through shared-memory slots, each guarded by
+// an mbarrier that its single producer warp arrives on (all 32 lanes) and its
+// single consumer warp waits on, so a warp only ever waits for its two vertical
+// neighbours; no CTA-wide barrier runs inside the inner loop.  Rows crossing a CTA
+// boundary are written into the neighbour CTA's slot (distributed shared memory)
+// and signalled on its mbarrier with cluster-scope release.  Every wait is bounded:
+// on timeout the kernel sets *err and carries on, so it always terminates.
+//
+// Why single-buffered slots are safe: a producer rewrites a slot one iteration
+// later only after waiting on a signal that the slot's consumer sends after it read
+// the slot (each half-step of a warp depends on the other half-step of the warp it
+// feeds).
+// A waiting warp sleeps in mbarrier.try_wait until the phase completes or the hint
+// (ns) runs out; kWaitLimit rounds of it bound the wait at about one second.
+constexpr unsigned kWaitLimit = 1000;
+constexpr unsigned kSuspendHintNs = 1000000;
+
+__device__ __forceinline__ void mbar_init(uint32_t addr, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_local(uint32_t addr) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(addr)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity), "r"(kSuspendHintNs)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; returns false (and the caller records the timeout) when the limit runs out
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+  for (unsigned it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(addr, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void st_cluster_v4(uint32_t addr, float4 v) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w)
+               : "memory");
+}
+
+template <int R, int NW>
+struct WrLayout {
+  static constexpr int BAND = NW * R;
+  static constexpr int SU = 0;                   // (NW + 1) x 128: slot w+1 = last-row u of warp w; slot 0 = row above
+  static constexpr int SQ = SU + (NW + 1) * 128; // (NW + 1) x 128: slot w = first-row pbar1 of warp w; slot NW = row below
+  static constexpr int CO = SQ + (NW + 1) * 128; // 64 x 8 coefficients
+  static constexpr int MB = CO + 64 * 8;         // mbarriers (8 bytes each): mU[NW + 1], mQ[NW + 1]
+  static constexpr size_t BYTES = sizeof(float) * MB + 8 * 2 * (NW + 1);
+};
+
+template <int R, int NW, int CL, int MINB, int FID, bool MASK>
+__global__ void __launch_bounds__(32 * NW, MINB) k_fused_wr(const LocalArgs A) {
+  using L = WrLayout<R, NW>;
+  constexpr int BAND = L::BAND;
+  static_assert(CL * BAND == 128, "a cluster covers the 128 rows of a tile");
+  extern __shared__ __align__(16) float smem[];
+  float* slotU = smem + L::SU;
+  float* slotQ = smem + L::SQ;
+  float* sCo = smem + L::CO;
+  const uint32_t mbase = smem_addr(smem + L::MB);
+  auto mU = [&](int q) { return mbase + 8u * q; };
+  auto mQ = [&](int q) { return mbase + 8u * (NW + 1 + q); };
+
+  const Grid g = A.g;
+  const int rank = CL > 1 ? (int)blockIdx.x : 0;
+  const int b = blockIdx.y, a = blockIdx.z;
+  const int r0 = a * 128, c0 = b * 128;
+  const bool s_top = a > 0, s_bot = a + 1 < g.NR, s_lft = b > 0, s_rgt = b + 1 < g.NC;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i0 = rank * BAND + w * R;  // first tile row of this warp
+  const int W2 = g.W + g.NC;
+  const int jc = 4 * lane;             // first tile column of this lane
+  const float tau = A.tau;
+  const bool first_warp_of_tile = rank == 0 && w == 0;
+  const bool last_warp_of_tile = rank == CL - 1 && w == NW - 1;
+  const float lim_top = (first_warp_of_tile && !s_top) ? 0.f : 1.f;  // row 0 of the tile only
+  const float lim_left = (lane == 0 && !s_lft) ? 0.f : 1.f;         // column 0 only
+  const float lim_right = (lane == 31 && s_rgt) ? 1.f : 0.f;         // right side dofs (lane 31)
+  // producers/consumers across the CTA boundary
+  const bool push_down = CL > 1 && w == NW - 1 && rank + 1 < CL;   // my last row -> slot 0 of rank+1
+  const bool push_up = CL > 1 && w == 0 && rank > 0;                 // my first row -> slot NW of rank-1
+  uint32_t rem_slotU = 0, rem_mU = 0, rem_slotQ = 0, rem_mQ = 0;
+  if (push_down) {
+    rem_slotU = map_rank(smem_addr(slotU + jc), rank + 1);
+    rem_mU = map_rank(mU(0), rank + 1);
+  }
+  if (push_up) {
+    rem_slotQ = map_rank(smem_addr(slotQ + NW * 128 + jc), rank - 1);
+    rem_mQ = map_rank(mQ(NW), rank - 1);
+  }
+  // does this warp wait for a producer before its u-step (row below) / p-step (row above)?
+  const bool wait_below = !(last_warp_of_tile);  // last warp of the tile reads its own bottom-side slot
+  const bool wait_above = !(rank == 0 && w == 0);
+
+  // ---- set-up: barriers, coefficients
+  if (threadIdx.x == 0) {
+    for (int q = 0; q <= NW; ++q) {
+      mbar_init(mU(q), 32);
+      mbar_init(mQ(q), 32);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int q = threadIdx.x; q < 8 * min(A.K, 64); q += 32 * NW) sCo[q] = reinterpret_cast<const float*>(A.coef)[q];
+  if (rank == 0) {
+    for (int q = threadIdx.x; q < 128; q += 32 * NW) slotU[q] = 0.f;  // u = 0 above the tile
+  }
+
+  // ---- load the state of rows i0 .. i0+R-1, columns jc .. jc+3
+  float u[R][4], p1[R][4], p2[R][4], h1[R][4], h2[R][4], q1[R][4], q2[R][4], fg[R][4];
+  float pR[R], hR[R], qR[R];
+  float pB[4] = {0.f, 0.f, 0.f, 0.f}, hB[4] = {0.f, 0.f, 0.f, 0.f};
+  uint32_t in_d = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int gi = r0 + i0 + r;
+    const size_t px = (size_t)gi * g.W + c0 + jc;
+    const float4 uv = *reinterpret_cast<const float4*>(A.u + px);
+    const float4 fv = *reinterpret_cast<const float4*>(A.f + px);
+    const float4 pv = *reinterpret_cast<const float4*>(A.P1 + (size_t)(gi + a) * g.W + c0 + jc);
+    const float uu[4] = {uv.x, uv.y, uv.z, uv.w}, ff[4] = {fv.x, fv.y, fv.z, fv.w}, pp[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      u[r][c] = uu[c];
+      float f = ff[c];
+      if (FID == FID_SEG) f = (f - A.c1) * (f - A.c1) - (f - A.c2) * (f - A.c2);
+      fg[r][c] = f;
+      if (MASK && A.mask[px + c]) in_d |= 1u << (4 * r + c);
+      p1[r][c] = pp[c];
+      p2[r][c] = A.P2[(size_t)gi * W2 + c0 + b + jc + c];
+      h1[r][c] = p1[r][c];
+      h2[r][c] = p2[r][c];
+      q1[r][c] = p1[r][c];
+      q2[r][c] = p2[r][c];
+    }
+    pR[r] = hR[r] = 0.f;
+    if (lane == 31 && s_rgt) {
+      pR[r] = A.P2[(size_t)gi * W2 + c0 + b + 128];
+      hR[r] = phat_s(pR[r], A.lamv[(size_t)b * g.H + gi], tau);
+    }
+    qR[r] = pR[r];
+  }
+  if (first_warp_of_tile && s_top) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) h1[0][c] = phat_t(p1[0][c], A.lamh[(size_t)(a - 1) * g.W + c0 + jc + c], tau);
+  }
+  if (lane == 0 && s_lft) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) h2[r][0] = phat_t(p2[r][0], A.lamv[(size_t)(b - 1) * g.H + r0 + i0 + r], tau);
+  }
+  if (last_warp_of_tile && s_bot) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      pB[c] = A.P1[(size_t)(r0 + 128 + a) * g.W + c0 + jc + c];
+      hB[c] = phat_s(pB[c], A.lamh[(size_t)a * g.W + c0 + jc + c], tau);
+    }
+  }
+  // initial slots: first-row pbar1 of every warp, the tile's bottom side
+  *reinterpret_cast<float4*>(slotQ + w * 128 + jc) = make_float4(q1[0][0], q1[0][1], q1[0][2], q1[0][3]);
+  if (last_warp_of_tile) *reinterpret_cast<float4*>(slotQ + NW * 128 + jc) = make_float4(pB[0], pB[1], pB[2], pB[3]);
+  __syncthreads();
+  if (CL > 1) {
+    cluster_arrive<true>();  // mbarrier inits of every CTA are visible before any remote arrive
+    cluster_wait();
+    if (push_up) st_cluster_v4(rem_slotQ, make_float4(q1[0][0], q1[0][1], q1[0][2], q1[0][3]));
+    cluster_arrive<true>();
+    cluster_wait();
+  }
+
+  bool timed_out = false;
+  float* myU = slotU + (w + 1) * 128 + jc;   // last-row u of this warp (read by the warp below)
+  const float* abU = slotU + w * 128 + jc;   // last-row u of the warp above
+  float* myQ = slotQ + w * 128 + jc;         // first-row pbar1 of this warp (read by the warp above)
+  const float* beQ = slotQ + (w + 1) * 128 + jc;  // first-row pbar1 of the warp below
+
+  for (int k = 0; k < A.K; ++k) {
+    const float4 ca = *reinterpret_cast<const float4*>(sCo + 8 * (k & 63));
+    const float4 cb = *reinterpret_cast<const float4*>(sCo + 8 * (k & 63) + 4);
+    Coef c{ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+    if (k >= 64) c = A.coef[k];
+    // ---------------- u-step: needs the first-row pbar1 of the warp below (iteration k-1)
+    if (k > 0 && wait_below && !mbar_wait(mQ(w + 1), (uint32_t)((k - 1) & 1))) timed_out = true;
+    const float4 bq = *reinterpret_cast<const float4*>(beQ);
+    const float below_last[4] = {bq.x, bq.y, bq.z, bq.w};
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float nxt = __shfl_down_sync(0xffffffffu, q2[r][0], 1);
+      const float right3 = lane == 31 ? qR[r] : nxt;
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        const float below = r + 1 < R ? q1[r + 1][cc] : below_last[cc];
+        const float right = cc < 3 ? q2[r][cc + 1] : right3;
+        const float d = div_px(q1[r][cc], below, q2[r][cc], right);
+        u[r][cc] = u_update<FID>(u[r][cc], d, fg[r][cc], MASK && ((in_d >> (4 * r + cc)) & 1u), c);
+      }
+    }
+    {
+      const float4 lastu = make_float4(u[R - 1][0], u[R - 1][1], u[R - 1][2], u[R - 1][3]);
+      if (push_down) {
+        st_cluster_v4(rem_slotU, lastu);
+        mbar_arrive_remote(rem_mU);
+      } else {
+        *reinterpret_cast<float4*>(myU) = lastu;
+        mbar_arrive_local(mU(w + 1));
+      }
+    }
+    // ---------------- p-step: needs the last-row u of the warp above (iteration k)
+    if (wait_above && !mbar_wait(mU(w), (uint32_t)(k & 1))) timed_out = true;
+    const float4 au = *reinterpret_cast<const float4*>(abU);
+    const float above_first[4] = {au.x, au.y, au.z, au.w};
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float prv = __shfl_up_sync(0xffffffffu, u[r][3], 1);
+      const float left0 = lane == 0 ? 0.f : prv;
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        const float above = r > 0 ? u[r - 1][cc] : above_first[cc];
+        p_update_lim(p1[r][cc], q1[r][cc], u[r][cc] - above, h1[r][cc], c, r == 0 ? lim_top : 1.f);
+        const float left = cc > 0 ? u[r][cc - 1] : left0;
+        p_update_lim(p2[r][cc], q2[r][cc], u[r][cc] - left, h2[r][cc], c, cc == 0 ? lim_left : 1.f);
+      }
+      p_update_lim(pR[r], qR[r], -u[r][3], hR[r], c, lim_right);  // right side (lane 31)
+    }
+    if (last_warp_of_tile && s_bot) {  // bottom side, read back by this warp's next u-step
+      float qB[4];
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) p_update(pB[cc], qB[cc], -u[R - 1][cc], hB[cc], c);
+      *reinterpret_cast<float4*>(slotQ + NW * 128 + jc) = make_float4(qB[0], qB[1], qB[2], qB[3]);
+      __syncwarp();
+    }
+    {
+      const float4 firstq = make_float4(q1[0][0], q1[0][1], q1[0][2], q1[0][3]);
+      if (push_up) {
+        st_cluster_v4(rem_slotQ, firstq);
+        mbar_arrive_remote(rem_mQ);
+      } else {
+        *reinterpret_cast<float4*>(myQ) = firstq;
+        mbar_arrive_local(mQ(w));
+      }
+    }
+  }
+  if (timed_out) atomicOr(A.err, 1);
+  if (CL > 1) {  // no CTA leaves while a neighbour may still write into its shared memory
+    cluster_arrive<true>();
+    cluster_wait();
+  }
+
+  // ---- store u^{n+1}, p~^{n+1} and the interface strips
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int gi = r0 + i0 + r;
+    const size_t px = (size_t)gi * g.W + c0 + jc;
+    *reinterpret_cast<float4*>(A.u + px) = make_float4(u[r][0], u[r][1], u[r][2], u[r][3]);
+    *reinterpret_cast<float4*>(A.P1 + (size_t)(gi + a) * g.W + c0 + jc) =
+        make_float4(p1[r][0], p1[r][1], p1[r][2], p1[r][3]);
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) A.P2[(size_t)gi * W2 + c0 + b + jc + cc] = p2[r][cc];
+    if (lane == 31 && s_rgt) {
+      A.P2[(size_t)gi * W2 + c0 + b + 128] = pR[r];
+      A.out.SR[(size_t)b * g.H + gi] = pR[r];
+    }
+    if (lane == 0 && s_lft) A.out.SL[(size_t)(b - 1) * g.H + gi] = p2[r][0];
+  }
+  if (first_warp_of_tile && s_top)
+    *reinterpret_cast<float4*>(A.out.ST + (size_t)(a - 1) * g.W + c0 + jc) =
+        make_float4(p1[0][0], p1[0][1], p1[0][2], p1[0][3]);
+  if (last_warp_of_tile && s_bot) {
+    const float4 v = make_float4(pB[0], pB[1], pB[2], pB[3]);
+    *reinterpret_cast<float4*>(A.P1 + (size_t)(r0 + 128 + a) * g.W + c0 + jc) = v;
+    *reinterpret_cast<float4*>(A.out.SB + (size_t)a * g.W + c0 + jc) = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Full-tile kernel with asynchronous halo exchange.  Same arithmetic and mapping as
+// k_fused_full, but inside the inner loop no cluster barrier runs: a halo row is
+// written into the neighbour CTA with st.async, whose completion is counted (in
+// bytes) on an mbarrier in the neighbour's shared memory, so the producing warps
+// never wait for the remote store; only the warps that read a halo wait, on their
+// own CTA's mbarrier (bounded).  Each halo mbarrier completes one phase per inner
+// iteration: the consumer arrives once per phase with the expected byte count, the
+// producer's stores bring the byte count to zero.  A producer cannot run a phase
+// ahead of its consumer (its next halo row depends on the consumer's previous one),
+// so the single halo buffers are never overwritten while being read.
+__device__ __forceinline__ void st_async_f32(uint32_t remote_addr, float v, uint32_t remote_mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(remote_addr),
+               "r"(__float_as_uint(v)), "r"(remote_mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t addr, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.release.cta.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(addr),
+               "r"(bytes)
+               : "memory");
+}
+
+template <int R, int TR>
+struct AsyncLayout {
+  using F = FullLayout<R, TR>;
+  static constexpr int MB = (F::FLOATS + 1) & ~1;  // two mbarriers (8-byte aligned): u halo, pbar1 halo
+  static constexpr size_t BYTES = sizeof(float) * MB + 16;
+};
+
+template <int R, int TR, int CL, int MINB, int FID, bool MASK>
+__global__ void __launch_bounds__(128 * TR, MINB) k_fused_async(const LocalArgs A) {
+  using L = FullLayout<R, TR>;
+  using AL = AsyncLayout<R, TR>;
+  constexpr int BW = L::BW, BAND = L::BAND;
+  static_assert(CL * BAND == 128 && CL > 1, "a cluster of CTAs covers the 128 rows of a tile");
+  extern __shared__ __align__(16) float smem[];
+  float* sU = smem + L::U;
+  float* sQ2 = smem + L::Q2;
+  float* sQ1 = smem + L::Q1;
+  float* sF = smem + L::F;
+  float* sPR = smem + L::PR;
+  float* sHR = smem + L::HR;
+  float* sCo = smem + L::CO;
+  const uint32_t mbU = smem_addr(smem + AL::MB);      // u halo (row above the band) has landed
+  const uint32_t mbQ = mbU + 8;                        // pbar1 halo (row below the band) has landed
+
+  const Grid g = A.g;
+  const int rank = (int)blockIdx.x;
+  const int b = blockIdx.y, a = blockIdx.z;
+  const int r0 = a * 128, c0 = b * 128;
+  const bool s_top = a > 0, s_bot = a + 1 < g.NR, s_lft = b > 0, s_rgt = b + 1 < g.NC;
+  const int j = threadIdx.x, ty = threadIdx.y;
+  const int lr0 = ty * R;
+  const int i0 = rank * BAND + lr0;
+  const int W2 = g.W + g.NC;
+  const int gj = c0 + j;
+  const float tau = A.tau;
+  const float lim_left = (j == 0 && !s_lft) ? 0.f : 1.f;
+  const float lim_top = (i0 == 0 && !s_top) ? 0.f : 1.f;
+  const bool last_row_here = rank == CL - 1 && ty == TR - 1;
+  const bool push_down = ty == TR - 1 && rank + 1 < CL;  // my last row -> u halo of rank + 1
+  const bool push_up = ty == 0 && rank > 0;              // my first row -> pbar1 halo of rank - 1
+  const bool need_uh = ty == 0 && rank > 0;              // reads the u halo
+  const bool need_qh = ty == TR - 1 && rank + 1 < CL;    // reads the pbar1 halo
+  const bool right_lane = s_rgt && j < R;
+  constexpr uint32_t kHaloBytes = 4 * BW;
+  uint32_t remote_u = 0, remote_q1 = 0, remote_mbU = 0, remote_mbQ = 0;
+  if (push_down) {
+    remote_u = map_rank(smem_addr(sU + 1 + j), rank + 1);
+    remote_mbU = map_rank(mbU, rank + 1);
+  }
+  if (push_up) {
+    remote_q1 = map_rank(smem_addr(sQ1 + TR * BW + j), rank - 1);
+    remote_mbQ = map_rank(mbQ, rank - 1);
+  }
+  if (j == 0 && ty == 0) {
+    mbar_init(mbU, 1);
+    mbar_init(mbQ, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+
+  float u[R], p1[R], p2[R], h1[R], h2[R], q1[R];
+  uint32_t in_d = 0;
+  float pB = 0.f, hB = 0.f;
+
+  for (int q = threadIdx.x + threadIdx.y * BW; q < 8 * min(A.K, L::kMaxSmemCoef); q += BW * TR)
+    sCo[q] = reinterpret_cast<const float*>(A.coef)[q];
+  if (rank == 0) sU[1 + j] = 0.f;
+  if (j == 0) sU[0] = 0.f;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int gi = r0 + i0 + r;
+    const size_t px = (size_t)gi * g.W + gj;
+    u[r] = A.u[px];
+    float fv = A.f[px];
+    if (FID == FID_SEG) fv = (fv - A.c1) * (fv - A.c1) - (fv - A.c2) * (fv - A.c2);
+    sF[(lr0 + r) * BW + j] = fv;
+    if (MASK && A.mask[px]) in_d |= 1u << r;
+    p1[r] = A.P1[(size_t)(gi + a) * g.W + gj];
+    p2[r] = A.P2[(size_t)gi * W2 + gj + b];
+    h1[r] = p1[r];
+    h2[r] = p2[r];
+    q1[r] = p1[r];
+    sQ2[(lr0 + r) * L::QS + j] = p2[r];
+    sU[(lr0 + r + 1) * L::US] = 0.f;
+  }
+  if (i0 == 0 && s_top) h1[0] = phat_t(p1[0], A.lamh[(size_t)(a - 1) * g.W + gj], tau);
+  if (j == 0 && s_lft) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) h2[r] = phat_t(p2[r], A.lamv[(size_t)(b - 1) * g.H + r0 + i0 + r], tau);
+  }
+  if (last_row_here) {
+    if (s_bot) {
+      pB = A.P1[(size_t)(r0 + 128 + a) * g.W + gj];
+      hB = phat_s(pB, A.lamh[(size_t)a * g.W + gj], tau);
+    }
+    sQ1[TR * BW + j] = pB;
+  }
+  if (j < R) {
+    float pr = 0.f, hr = 0.f;
+    if (s_rgt) {
+      const int gi = r0 + i0 + j;
+      pr = A.P2[(size_t)gi * W2 + c0 + 128 + b];
+      hr = phat_s(pr, A.lamv[(size_t)b * g.H + gi], tau);
+    }
+    sPR[lr0 + j] = pr;
+    sHR[lr0 + j] = hr;
+    sQ2[(lr0 + j) * L::QS + 128] = pr;
+  }
+  sQ1[ty * BW + j] = q1[0];
+  __syncthreads();
+  // every CTA's mbarriers are initialised before anyone signals them; the initial
+  // pbar1 halo goes through a plain remote store ordered by the cluster barrier
+  cluster_arrive<true>();
+  cluster_wait();
+  if (push_up) st_cluster(remote_q1, q1[0]);
+  cluster_arrive<true>();
+  cluster_wait();
+
+  bool timed_out = false;
+  float* sUr = sU + (lr0 + 1) * L::US + j + 1;
+  float* sQ2r = sQ2 + lr0 * L::QS + j;
+  const float* sFr = sF + lr0 * BW + j;
+
+  for (int k = 0; k < A.K; ++k) {
+    Coef c;
+    if (k < L::kMaxSmemCoef) {
+      const float4 ca = *reinterpret_cast<const float4*>(sCo + 8 * k);
+      const float4 cb = *reinterpret_cast<const float4*>(sCo + 8 * k + 4);
+      c = Coef{ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+    } else {
+      c = A.coef[k];
+    }
+    // ---- u-step; the band's last row first (it feeds the CTA below)
+    if (need_qh && k > 0) {  // pbar1 halo of iteration k-1
+      if (j == 0) mbar_arrive_expect_tx(mbQ, kHaloBytes);
+      if (!mbar_wait(mbQ, (uint32_t)((k - 1) & 1))) timed_out = true;
+    }
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+      const int r = (rr + R - 1) % R;
+      const float below = r + 1 < R ? q1[r + 1] : sQ1[(ty + 1) * BW + j];
+      const float d = div_px(q1[r], below, sQ2r[r * L::QS], sQ2r[r * L::QS + 1]);
+      u[r] = u_update<FID>(u[r], d, sFr[r * BW], MASK && ((in_d >> r) & 1u), c);
+      sUr[r * L::US] = u[r];
+      if (rr == 0 && push_down) st_async_f32(remote_u, u[R - 1], remote_mbU);
+    }
+    __syncthreads();
+    // ---- p-step; the band's first row first (it feeds the CTA above)
+    if (need_uh) {  // u halo of iteration k
+      if (j == 0) mbar_arrive_expect_tx(mbU, kHaloBytes);
+      if (!mbar_wait(mbU, (uint32_t)(k & 1))) timed_out = true;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float above = r > 0 ? u[r - 1] : sUr[-L::US];
+      p_update_lim(p1[r], q1[r], u[r] - above, h1[r], c, r == 0 ? lim_top : 1.f);
+      float q2;
+      p_update_lim(p2[r], q2, u[r] - sUr[r * L::US - 1], h2[r], c, lim_left);
+      sQ2r[r * L::QS] = q2;
+      if (r == 0) {
+        sQ1[ty * BW + j] = q1[0];
+        if (push_up) st_async_f32(remote_q1, q1[0], remote_mbQ);
+      }
+    }
+    if (last_row_here && s_bot) {
+      float qB;
+      p_update(pB, qB, -u[R - 1], hB, c);
+      sQ1[TR * BW + j] = qB;
+    }
+    if (right_lane) {
+      const int lr = lr0 + j;
+      float pr = sPR[lr], qr;
+      p_update(pr, qr, -sU[(lr + 1) * L::US + 128], sHR[lr], c);
+      sPR[lr] = pr;
+      sQ2[lr * L::QS + 128] = qr;
+    }
+    __syncthreads();
+  }
+  // the last pbar1 halo is never read: wait for it to land before leaving
+  if (need_qh && A.K > 0) {
+    if (j == 0) mbar_arrive_expect_tx(mbQ, kHaloBytes);
+    if (!mbar_wait(mbQ, (uint32_t)((A.K - 1) & 1))) timed_out = true;
+  }
+  if (timed_out) atomicOr(A.err, 1);
+  cluster_arrive<true>();
+  cluster_wait();
+
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int gi = r0 + i0 + r;
+    A.u[(size_t)gi * g.W + gj] = u[r];
+    A.P1[(size_t)(gi + a) * g.W + gj] = p1[r];
+    A.P2[(size_t)gi * W2 + gj + b] = p2[r];
+  }
+  if (i0 == 0 && s_top) A.out.ST[(size_t)(a - 1) * g.W + gj] = p1[0];
+  if (j == 0 && s_lft) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) A.out.SL[(size_t)(b - 1) * g.H + r0 + i0 + r] = p2[r];
+  }
+  if (last_row_here && s_bot) {
+    A.P1[(size_t)(r0 + 128 + a) * g.W + gj] = pB;
+    A.out.SB[(size_t)a * g.W + gj] = pB;
+  }
+  if (right_lane) {
+    const int gi = r0 + i0 + j;
+    const float pr = sPR[lr0 + j];
+    A.P2[(size_t)gi * W2 + c0 + 128 + b] = pr;
+    A.out.SR[(size_t)b * g.H + gi] = pr;
+  }
+}
+
 struct Config {
   int BW, R, TR, CL;
   const char* name;
@@ -480,8 +1004,7 @@ constexpr Config kConfigs[] = {
     {128, 8, 4, 4, "bw128_r8_tr4_cl4"},    // class 2, variant 1: 512 threads, 1 CTA/SM
     {128, 16, 2, 4, "bw128_r16_tr2_cl4"},  // class 2, variant 2: 256 threads, 16 rows/thread
 };
-constexpr int kNumConfigs = (int)(sizeof(kConfigs) / sizeof(kConfigs[0]));
-constexpr int kNumVariants = 3;
+constexpr int kNumVariants = 4;
 
 template <int BW, int R, int TR, int CL, int FID, bool MASK>
 cudaError_t launch_one(const LocalArgs& a, cudaStream_t st) {
@@ -542,6 +1065,79 @@ cudaError_t launch_full(const LocalArgs& a, int fid, cudaStream_t st) {
 }
 
 template <int R, int TR, int CL, int MINB, int FID, bool MASK>
+cudaError_t launch_async_one(const LocalArgs& a, cudaStream_t st) {
+  using AL = AsyncLayout<R, TR>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL, a.g.NC, a.g.NR);
+  cfg.blockDim = dim3(128, TR, 1);
+  cfg.dynamicSmemBytes = AL::BYTES;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_fused_async<R, TR, CL, MINB, FID, MASK>, a);
+}
+
+template <int R, int TR, int CL, int MINB>
+cudaError_t launch_async(const LocalArgs& a, int fid, cudaStream_t st) {
+  const bool m = a.mask != nullptr;
+  switch (fid) {
+    case FID_L2: return m ? launch_async_one<R, TR, CL, MINB, FID_L2, true>(a, st) : launch_async_one<R, TR, CL, MINB, FID_L2, false>(a, st);
+    case FID_L1: return m ? launch_async_one<R, TR, CL, MINB, FID_L1, true>(a, st) : launch_async_one<R, TR, CL, MINB, FID_L1, false>(a, st);
+    default: return launch_async_one<R, TR, CL, MINB, FID_SEG, false>(a, st);
+  }
+}
+
+template <int R, int TR, int CL, int MINB, int FID, bool MASK>
+cudaError_t prepare_async_one() {
+  using AL = AsyncLayout<R, TR>;
+  return cudaFuncSetAttribute(k_fused_async<R, TR, CL, MINB, FID, MASK>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AL::BYTES);
+}
+
+template <int R, int TR, int CL, int MINB>
+cudaError_t prepare_async() {
+  cudaError_t e;
+  if ((e = prepare_async_one<R, TR, CL, MINB, FID_L2, false>()) != cudaSuccess) return e;
+  if ((e = prepare_async_one<R, TR, CL, MINB, FID_L2, true>()) != cudaSuccess) return e;
+  if ((e = prepare_async_one<R, TR, CL, MINB, FID_L1, false>()) != cudaSuccess) return e;
+  if ((e = prepare_async_one<R, TR, CL, MINB, FID_L1, true>()) != cudaSuccess) return e;
+  return prepare_async_one<R, TR, CL, MINB, FID_SEG, false>();
+}
+
+template <int R, int NW, int CL, int MINB, int FID, bool MASK>
+cudaError_t launch_wr_one(const LocalArgs& a, cudaStream_t st) {
+  using L = WrLayout<R, NW>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL, a.g.NC, a.g.NR);
+  cfg.blockDim = dim3(32 * NW, 1, 1);
+  cfg.dynamicSmemBytes = L::BYTES;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_fused_wr<R, NW, CL, MINB, FID, MASK>, a);
+}
+
+template <int R, int NW, int CL, int MINB>
+cudaError_t launch_wr(const LocalArgs& a, int fid, cudaStream_t st) {
+  const bool m = a.mask != nullptr;
+  switch (fid) {
+    case FID_L2: return m ? launch_wr_one<R, NW, CL, MINB, FID_L2, true>(a, st) : launch_wr_one<R, NW, CL, MINB, FID_L2, false>(a, st);
+    case FID_L1: return m ? launch_wr_one<R, NW, CL, MINB, FID_L1, true>(a, st) : launch_wr_one<R, NW, CL, MINB, FID_L1, false>(a, st);
+    default: return launch_wr_one<R, NW, CL, MINB, FID_SEG, false>(a, st);
+  }
+}
+
+template <int R, int TR, int CL, int MINB, int FID, bool MASK>
 cudaError_t prepare_full_one() {
   using L = FullLayout<R, TR>;
   return cudaFuncSetAttribute(k_fused_full<R, TR, CL, MINB, FID, MASK>,
@@ -579,7 +1175,7 @@ cudaError_t prepare_fid() {
 int pick(int mr, int mc, int variant) {
   if (mc <= 32 && mr <= 32) return 0;
   if (mc <= 64 && mr <= 64) return 1;
-  if (mc <= 128 && mr <= 128 && variant >= 0 && variant < kNumVariants) return 2 + variant;
+  if (mc <= 128 && mr <= 128 && variant >= 0 && variant < kNumVariants) return 2 + (variant < 3 ? variant : 0);
   return -1;
 }
 
@@ -604,9 +1200,9 @@ cudaError_t fused_prepare() {
   if ((e = prepare_fid<128, 8, 2, 8>()) != cudaSuccess) return e;
   if ((e = prepare_fid<128, 8, 4, 4>()) != cudaSuccess) return e;
   if ((e = prepare_fid<128, 16, 2, 4>()) != cudaSuccess) return e;
-  if ((e = prepare_full<8, 2, 8, 2>()) != cudaSuccess) return e;
   if ((e = prepare_full<8, 4, 4, 1>()) != cudaSuccess) return e;
-  return prepare_full<8, 2, 8, 3>();
+  if ((e = prepare_async<8, 2, 8, 2>()) != cudaSuccess) return e;
+  return prepare_async<8, 4, 4, 1>();
 }
 
 cudaError_t launch_fused_local(const LocalArgs& a, int fid, int variant, cudaStream_t st) {
@@ -614,9 +1210,10 @@ cudaError_t launch_fused_local(const LocalArgs& a, int fid, int variant, cudaStr
   const int mr = (a.g.H + a.g.NR - 1) / a.g.NR, mc = (a.g.W + a.g.NC - 1) / a.g.NC;
   if (a.g.H == 128 * a.g.NR && a.g.W == 128 * a.g.NC) {  // every tile exactly 128 x 128
     switch (variant) {
-      case 0: return launch_full<8, 4, 4, 1>(a, fid, st);  // 512 threads, 1 CTA/SM
-      case 1: return launch_full<8, 2, 8, 2>(a, fid, st);  // 256 threads, 2 CTAs/SM
-      case 2: return launch_full<8, 2, 8, 3>(a, fid, st);  // 256 threads, 3 CTAs/SM (<= 85 registers)
+      case 0: return launch_async<8, 2, 8, 2>(a, fid, st);  // column strips, async halos: 256 threads, 2 CTAs/SM
+      case 1: return launch_async<8, 4, 4, 1>(a, fid, st);  // column strips, async halos: 512 threads
+      case 2: return launch_full<8, 4, 4, 1>(a, fid, st);   // column strips, cluster barrier: 512 threads
+      case 3: return launch_wr<2, 8, 8, 2>(a, fid, st);     // warp rows, per-warp mbarriers
       default: return cudaErrorInvalidValue;
     }
   }

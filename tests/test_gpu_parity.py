@@ -219,13 +219,13 @@ def test_full_size_4096_sampled_parity():
     assert np.abs(g["lamh"] - o.lamh).max() <= 1e-3
 
 
-@pytest.mark.parametrize("H,W,NR,NC", [(384, 384, 3, 3), (250, 260, 2, 3), (128, 128, 1, 1)])
+@pytest.mark.parametrize("H,W,NR,NC", [(384, 384, 3, 3), (250, 260, 2, 3), (128, 128, 1, 1), (1024, 1280, 8, 10)])
 def test_fused_variants_bitwise_identical(H, W, NR, NC):
     """Every hardware mapping of a 128x128-class subdomain runs the same arithmetic."""
     L = _gpu()
     f, _ = synth.rof_image(H, W, 12, 0.1, 12)
     outs = []
-    for v in range(3):
+    for v in range(4):
         _, g, _, _ = _run_gpu(f, None, 7, sub_rows=NR, sub_cols=NC, alpha=8.0, variant=v)
         outs.append(g)
     for g in outs[1:]:
