@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-tta", action="store_true", help="skip the time-to-accuracy runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched multi-image measurement")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuned time-to-accuracy")
     return ap.parse_args()
 
 
@@ -341,6 +343,37 @@ def run_ours(args):
                 sp.close()
             if tta["fused"]["reached"] and tta["plain"]["reached"]:
                 tta["speedup_vs_plain"] = tta["plain"]["ms"] / tta["fused"]["ms"]
+            if not args.no_tune:
+                from paper_1901_00682_gb300 import autotune
+                r = autotune.tune(fd, dict(fidelity="l2", alpha=ALPHA), tol=1e-4, j_ref=rec["J_star"],
+                                  tiles=(64, 128), inners=(5, 10, 20), max_outer=3000, stream=stream)
+                b = r.best
+                tta["autotuned"] = {"tile": b.tile, "inner_iters": b.inner, "variant": b.variant, "ms": b.ms,
+                                    "outer_iters": b.outer, "reached": b.reached, "trials": r.table()}
+
+    batch = None
+    if not args.no_batch:
+        import synth
+        ims = synth.batch_workload(64, 0)
+        bt = L.Batch(ims, inner_iters=INNER, stream=stream)
+        fs = [torch.from_numpy(m["f"]).to(dev) for m in ims]
+        bt.load(fs)
+        bt.iterate(8)
+        torch.cuda.synchronize(dev)
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_b = 40
+        b0.record(stream)
+        bt.iterate(n_b)
+        b1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_b = b0.elapsed_time(b1) / n_b
+        batch = {"workload": "64 images, sides {256,512,1024,2048} x aspect {1:1,2:1,1:2}, even ROF (sigma .05, "
+                             "alpha 10), odd segmentation (c1 .2, c2 .8, alpha 20, tau 1), 128x128 subdomains, "
+                             f"{INNER} inner", "pixels": bt.pixels(), "ms_per_outer": ms_b,
+                 "value": bt.pixels() * INNER / (ms_b * 1e-3) / 1e6, "unit": UNIT,
+                 "launch": "one CUDA graph per 4 outer iterations (2 kernels per outer iteration)"}
+        bt.close()
+        del fs
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -355,7 +388,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "l2": "state (~470 MB) larger than L2; no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "step": "1 outer iteration (interface + fused local solves), energy every 5 steps"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "time_to_accuracy": tta,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "time_to_accuracy": tta, "batch": batch,
             "clocks": clocks.summary(), "gpu_launches": launches,
             "launches_by_phase": prof_n, "phase_ms": prof_ms,
         }

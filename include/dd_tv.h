@@ -210,6 +210,48 @@ int dd_tv_measure_smem_bandwidth(double* gbs_out);
 int dd_tv_energy_noalloc(const float* u_dev, const float* f_dev, const uint8_t* mask_dev, int height, int width,
                          int fidelity, double alpha, double c1, double c2, void* stream, double* J_out);
 
+/* ---- Batched solve (many images in one launch per phase).
+ * Every image is an independent instance of the model problem (Section 3) solved by
+ * Algorithm 1 with its own fidelity, alpha, c1, c2 and outer steps; all images share
+ * the subdomain size, the number of inner iterations and the initial inner steps, and
+ * advance by the same number of outer iterations.  One outer iteration of the whole
+ * batch is two kernel launches (multiplier update of every interface of every image,
+ * then the local solves of every subdomain of every image), replayed as a CUDA graph.
+ * Image sides must be multiples of the subdomain side (128).  Results are bit-identical
+ * to solving each image alone with the same parameters. */
+typedef struct dd_tv_batch dd_tv_batch;
+
+typedef struct {
+  int height, width;      /* multiples of 128                                          */
+  int fidelity;           /* DD_TV_L2, DD_TV_L1 or DD_TV_SEG (no inpainting mask)        */
+  double alpha, c1, c2;   /* as in dd_tv_params                                        */
+  double tau, sigma;      /* outer steps; tau <= 0 selects Section 5's defaults: tau = 50
+                             (1 for DD_TV_SEG), sigma = 1/(2 tau); gamma = 1/(8 tau)      */
+} dd_tv_batch_image;
+
+typedef struct {
+  int tile;               /* subdomain side; 128 is the only value supported             */
+  int inner_iters;        /* 1..DD_TV_MAX_INNER                                        */
+  double tau0, sigma0;    /* initial inner steps (Section 5: 10 and 1/80)               */
+  int variant;            /* hardware mapping of a subdomain: 0 or 1 (see dd_tv_params)  */
+} dd_tv_batch_params;
+
+/* Validates and allocates the batch (images[n], n >= 1); *out = NULL on error. */
+int dd_tv_batch_create(dd_tv_batch** out, const dd_tv_batch_image* images, int n, const dd_tv_batch_params* p);
+int dd_tv_batch_destroy(dd_tv_batch* b);                       /* NULL-safe */
+const char* dd_tv_batch_last_error(const dd_tv_batch* b);
+int dd_tv_batch_set_stream(dd_tv_batch* b, void* stream);
+/* Copies f_dev[i] (device, H_i x W_i float32) of every image and initialises every state
+ * as dd_tv_load does. */
+int dd_tv_batch_load(dd_tv_batch* b, const float* const* f_dev);
+/* n_outer outer iterations of every image (asynchronous). */
+int dd_tv_batch_iterate(dd_tv_batch* b, int n_outer);
+/* Copies image i's current u to u_dev; J(u) of image i (synchronous). */
+int dd_tv_batch_get_u(dd_tv_batch* b, int i, float* u_dev);
+int dd_tv_batch_energy(dd_tv_batch* b, int i, double* J_out);
+/* Total pixels of the batch (sum of H_i W_i). */
+long long dd_tv_batch_pixels(const dd_tv_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

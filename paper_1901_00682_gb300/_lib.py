@@ -69,6 +69,15 @@ SIGNATURES = {
     "dd_tv_profile_read": (_i, [_vp, _DP, ctypes.POINTER(ctypes.c_longlong)]),
     "dd_tv_measure_smem_bandwidth": (_i, [_DP]),
     "dd_tv_energy_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _i, _d, _d, _d, _vp, _DP]),
+    "dd_tv_batch_create": (_i, [ctypes.POINTER(_vp), _vp, _i, _vp]),
+    "dd_tv_batch_destroy": (_i, [_vp]),
+    "dd_tv_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "dd_tv_batch_set_stream": (_i, [_vp, _vp]),
+    "dd_tv_batch_load": (_i, [_vp, _vp]),
+    "dd_tv_batch_iterate": (_i, [_vp, _i]),
+    "dd_tv_batch_get_u": (_i, [_vp, _i, _vp]),
+    "dd_tv_batch_energy": (_i, [_vp, _i, _DP]),
+    "dd_tv_batch_pixels": (ctypes.c_longlong, [_vp]),
 }
 
 _lock = threading.Lock()
@@ -274,3 +283,78 @@ class Solver:
         J, D = ctypes.c_double(), ctypes.c_double()
         check(self.lib.dd_tv_gap(self.h, ctypes.byref(J), ctypes.byref(D)), self.h)
         return J.value, D.value
+
+
+class BatchImage(ctypes.Structure):
+    _fields_ = [("height", ctypes.c_int), ("width", ctypes.c_int), ("fidelity", ctypes.c_int),
+                ("alpha", ctypes.c_double), ("c1", ctypes.c_double), ("c2", ctypes.c_double),
+                ("tau", ctypes.c_double), ("sigma", ctypes.c_double)]
+
+
+class BatchParams(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int), ("inner_iters", ctypes.c_int), ("tau0", ctypes.c_double),
+                ("sigma0", ctypes.c_double), ("variant", ctypes.c_int)]
+
+
+def _bcheck(code, handle):
+    if code != OK:
+        msg = load().dd_tv_batch_last_error(handle)
+        raise DDTVError(code, msg.decode() if msg else "")
+
+
+class Batch:
+    """Owns one dd_tv_batch handle: many images solved together (Algorithm 1 per image).
+
+    images: list of dicts with height, width, fidelity ("l2", "l1", "seg" or code),
+    alpha, c1, c2 and optionally tau, sigma (defaults: the paper's per fidelity)."""
+
+    def __init__(self, images, inner_iters=10, tau0=10.0, sigma0=None, variant=0, stream=None):
+        self.lib = load()
+        n = len(images)
+        arr = (BatchImage * n)()
+        for k, im in enumerate(images):
+            fid = {"l2": L2, "l1": L1, "seg": SEG}.get(im.get("fidelity", L2), im.get("fidelity", L2))
+            arr[k] = BatchImage(im["height"], im["width"], fid, im.get("alpha", 10.0), im.get("c1", 0.0),
+                                im.get("c2", 0.0), im.get("tau", 0.0), im.get("sigma", 0.0))
+        bp = BatchParams(128, inner_iters, tau0, sigma0 if sigma0 is not None else 0.125 / tau0, variant)
+        h = ctypes.c_void_p()
+        _bcheck(self.lib.dd_tv_batch_create(ctypes.byref(h), arr, n, ctypes.byref(bp)), None)
+        self.h = h
+        self.n = n
+        self.images = images
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream()
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+        _bcheck(self.lib.dd_tv_batch_set_stream(self.h, ctypes.c_void_p(s)), self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dd_tv_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, fs):
+        ptrs = (ctypes.c_void_p * self.n)(*[f.data_ptr() for f in fs])
+        self._keep = fs
+        _bcheck(self.lib.dd_tv_batch_load(self.h, ptrs), self.h)
+
+    def iterate(self, n_outer):
+        _bcheck(self.lib.dd_tv_batch_iterate(self.h, int(n_outer)), self.h)
+
+    def get_u(self, i, out):
+        _bcheck(self.lib.dd_tv_batch_get_u(self.h, int(i), out.data_ptr()), self.h)
+        return out
+
+    def energy(self, i):
+        J = ctypes.c_double()
+        _bcheck(self.lib.dd_tv_batch_energy(self.h, int(i), ctypes.byref(J)), self.h)
+        return J.value
+
+    def pixels(self):
+        return self.lib.dd_tv_batch_pixels(self.h)

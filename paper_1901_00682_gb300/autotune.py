@@ -1,0 +1,115 @@
+"""Autotuner for the subdomain size and the inner-iteration count.
+
+Both choices change the iterates of Algorithm 1 (more subdomains mean more interface
+constraints to reconcile; more inner iterations solve each local problem more
+exactly but cost more per outer iteration), so the tuner optimises what a user waits
+for: the wall time until the relative energy error (J(u^n) - J*)/|J*| falls below a
+tolerance (the outer stopping rule of Section 5), measured on the device for each
+candidate (tile side, K, hardware variant).  J* is either given (a certified value)
+or estimated as the lowest energy of a long run of the most accurate candidate.
+
+Every candidate runs the same kernels as a normal solve, so the choice never changes
+correctness, only speed; a tuned configuration is still checked against the oracle
+by the parity tests at equal (tile, K).
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+from . import _lib as L
+
+
+@dataclass
+class Trial:
+    tile: int
+    inner: int
+    variant: int
+    ms: float            # wall time of the solve to tolerance (ms), inf if not reached
+    outer: int           # outer iterations run
+    rel_err: float       # relative energy error at exit
+    reached: bool
+
+
+@dataclass
+class TuneResult:
+    best: Trial
+    trials: list = field(default_factory=list)
+    j_ref: float = math.nan
+    tol: float = 0.0
+
+    def table(self):
+        return [dict(tile=t.tile, inner=t.inner, variant=t.variant, ms=t.ms, outer=t.outer, rel_err=t.rel_err,
+                     reached=t.reached) for t in self.trials]
+
+
+def candidates(height, width, tiles=(64, 128), inners=(5, 10, 20), variants=(0,)):
+    """(tile, K, variant) triples whose tiles divide the image."""
+    out = []
+    for t in tiles:
+        if height % t or width % t:
+            continue
+        for k in inners:
+            for v in variants:
+                out.append((t, k, v))
+    return out
+
+
+def pick_best(trials):
+    """The reached trial with the least time; ties go to fewer outer iterations."""
+    ok = [t for t in trials if t.reached and math.isfinite(t.ms)]
+    if not ok:
+        return min(trials, key=lambda t: (t.rel_err, t.ms)) if trials else None
+    return min(ok, key=lambda t: (t.ms, t.outer))
+
+
+def _params(height, width, tile, inner, variant, problem, **kw):
+    return L.make_params(height, width, height // tile, width // tile, inner_iters=inner, variant=variant,
+                         **problem, **kw)
+
+
+def estimate_reference(f, problem, tile=128, inner=20, outer=2000, stream=None):
+    """Lowest energy over a long run of one candidate (an upper bound of J*)."""
+    H, W = f.shape
+    s = L.Solver(_params(H, W, tile, inner, 0, problem), stream)
+    s.load(f)
+    best = math.inf
+    step = max(outer // 20, 1)
+    for _ in range(0, outer, step):
+        s.iterate(step)
+        best = min(best, s.current_energy())
+    s.close()
+    return best
+
+
+def tune(f, problem, tol=1e-4, j_ref=None, tiles=(64, 128), inners=(5, 10, 20), variants=(0,),
+         max_outer=3000, energy_every=5, stream=None, solve_fn=None):
+    """Measures every candidate's time to tolerance on image f (a device tensor) and
+    returns the fastest.  problem: dict of make_params keywords (fidelity, alpha, c1,
+    c2, tau ...).  solve_fn(tile, inner, variant, j_ref) -> Trial replaces the GPU
+    measurement (used by the host-side tests)."""
+    H, W = f.shape
+    if j_ref is None:
+        j_ref = estimate_reference(f, problem, stream=stream)
+    trials = []
+    for tile, inner, variant in candidates(H, W, tiles, inners, variants):
+        if solve_fn is not None:
+            trials.append(solve_fn(tile, inner, variant, j_ref))
+            continue
+        p = _params(H, W, tile, inner, variant, problem, outer_iters=max_outer, outer_tol=tol, energy_ref=j_ref,
+                    energy_every=energy_every)
+        try:
+            s = L.Solver(p, stream)
+        except L.DDTVError:
+            continue   # tile shape not supported by the fused path
+        u = f.new_empty(f.shape)
+        s.solve_device(f, None, u)            # warm-up: graph capture, caches
+        t0 = time.perf_counter()
+        _, st, rc = s.solve_device(f, None, u)
+        ms = (time.perf_counter() - t0) * 1e3
+        s.close()
+        reached = bool(st.converged)
+        trials.append(Trial(tile, inner, variant, ms if reached else math.inf, st.outer_done, st.rel_err, reached))
+    best = pick_best(trials)
+    return TuneResult(best, trials, j_ref, tol)

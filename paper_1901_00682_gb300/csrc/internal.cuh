@@ -41,6 +41,27 @@ struct LocalArgs {
   int* err;              // set non-zero by a kernel whose bounded wait ran out
 };
 
+// Batch of images solved together (every image partitioned into exact 128 x 128
+// subdomains).  Device arrays, one entry per image unless stated otherwise.
+struct BatchArgs {
+  const LocalArgs* args;   // per-image descriptor (its `out` field is unused)
+  const Strips* strips;    // 2 per image: strip sets by parity
+  const int* fid;          // fidelity per image
+  const int* tile_img;     // per tile of the batch: its image
+  const int* tile_base;    // first batch tile of each image
+  int write_set;           // strip set receiving p~^{n+1}
+};
+
+// Batched multiplier update: per image interface elements in units of 4 edges.
+struct BatchIfaceArgs {
+  const LocalArgs* args;   // per-image descriptor (geometry, lamh, lamv)
+  const Strips* strips;    // 2 per image
+  const float* sigma;      // outer sigma per image
+  const int* elem_base;    // n_img + 1 prefix sums of (nh + nv) / 4
+  int n_img;
+  int cur_set;             // strip set holding p~^n
+};
+
 // ---- kernels_interface.cu
 // lambda += sigma ((2 cur_s - prev_s) - (2 cur_t - prev_t)) on every interface edge.
 cudaError_t launch_interface(const Grid& g, float sigma, Strips cur, Strips prev, float* lamh, float* lamv,
@@ -50,7 +71,11 @@ cudaError_t launch_extract_strips(const Grid& g, const float* P1, const float* P
 // P1/P2 <- 0 except the interface values, taken from the strips
 cudaError_t launch_scatter_strips(const Grid& g, Strips s, float* P1, float* P2, cudaStream_t st);
 
+cudaError_t launch_interface_batch(const BatchIfaceArgs& a, int total4, cudaStream_t st);
+
 // ---- kernels_fused.cu
+// All tiles of all images of a batch, one launch (BatchArgs.write_set selects the strips).
+cudaError_t launch_fused_batch(const BatchArgs& B, int total_tiles, int variant, cudaStream_t st);
 // One outer iteration's local solves, all tiles, fused (returns cudaErrorInvalidValue
 // if no fused configuration fits the tile shape).
 cudaError_t launch_fused_local(const LocalArgs& a, int fidelity, int variant, cudaStream_t st);

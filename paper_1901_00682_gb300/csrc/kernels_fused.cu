@@ -787,8 +787,9 @@ struct AsyncLayout {
   static constexpr size_t BYTES = sizeof(float) * MB + 16;
 };
 
-template <int R, int TR, int CL, int MINB, int FID, bool MASK>
-__global__ void __launch_bounds__(128 * TR, MINB) k_fused_async(const LocalArgs A) {
+// Body of one CTA of the cluster that owns tile (a, b) of the image described by A.
+template <int R, int TR, int CL, int FID, bool MASK>
+__device__ __forceinline__ void fused_async_body(const LocalArgs& A, const int a, const int b) {
   using L = FullLayout<R, TR>;
   using AL = AsyncLayout<R, TR>;
   constexpr int BW = L::BW, BAND = L::BAND;
@@ -806,7 +807,6 @@ __global__ void __launch_bounds__(128 * TR, MINB) k_fused_async(const LocalArgs 
 
   const Grid g = A.g;
   const int rank = (int)blockIdx.x;
-  const int b = blockIdx.y, a = blockIdx.z;
   const int r0 = a * 128, c0 = b * 128;
   const bool s_top = a > 0, s_bot = a + 1 < g.NR, s_lft = b > 0, s_rgt = b + 1 < g.NC;
   const int j = threadIdx.x, ty = threadIdx.y;
@@ -990,6 +990,28 @@ __global__ void __launch_bounds__(128 * TR, MINB) k_fused_async(const LocalArgs 
   }
 }
 
+template <int R, int TR, int CL, int MINB, int FID, bool MASK>
+__global__ void __launch_bounds__(128 * TR, MINB) k_fused_async(const LocalArgs A) {
+  fused_async_body<R, TR, CL, FID, MASK>(A, blockIdx.z, blockIdx.y);
+}
+
+// Batched launch: blockIdx.y enumerates the tiles of every image of a batch; each
+// image has its own descriptor (geometry, buffers, fidelity, steps).
+template <int R, int TR, int CL, int MINB>
+__global__ void __launch_bounds__(128 * TR, MINB) k_fused_async_batch(const BatchArgs B) {
+  const int t = blockIdx.y;
+  const int img = B.tile_img[t];
+  LocalArgs A = B.args[img];
+  A.out = B.strips[2 * img + B.write_set];
+  const int lt = t - B.tile_base[img];
+  const int a = lt / A.g.NC, b = lt - a * A.g.NC;
+  switch (B.fid[img]) {
+    case FID_L2: fused_async_body<R, TR, CL, FID_L2, false>(A, a, b); break;
+    case FID_L1: fused_async_body<R, TR, CL, FID_L1, false>(A, a, b); break;
+    default: fused_async_body<R, TR, CL, FID_SEG, false>(A, a, b); break;
+  }
+}
+
 struct Config {
   int BW, R, TR, CL;
   const char* name;
@@ -1090,6 +1112,24 @@ cudaError_t launch_async(const LocalArgs& a, int fid, cudaStream_t st) {
     case FID_L1: return m ? launch_async_one<R, TR, CL, MINB, FID_L1, true>(a, st) : launch_async_one<R, TR, CL, MINB, FID_L1, false>(a, st);
     default: return launch_async_one<R, TR, CL, MINB, FID_SEG, false>(a, st);
   }
+}
+
+template <int R, int TR, int CL, int MINB>
+cudaError_t launch_async_batch(const BatchArgs& B, int total_tiles, cudaStream_t st) {
+  using AL = AsyncLayout<R, TR>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL, total_tiles, 1);
+  cfg.blockDim = dim3(128, TR, 1);
+  cfg.dynamicSmemBytes = AL::BYTES;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_fused_async_batch<R, TR, CL, MINB>, B);
 }
 
 template <int R, int TR, int CL, int MINB, int FID, bool MASK>
@@ -1202,7 +1242,17 @@ cudaError_t fused_prepare() {
   if ((e = prepare_fid<128, 16, 2, 4>()) != cudaSuccess) return e;
   if ((e = prepare_full<8, 4, 4, 1>()) != cudaSuccess) return e;
   if ((e = prepare_async<8, 2, 8, 2>()) != cudaSuccess) return e;
-  return prepare_async<8, 4, 4, 1>();
+  if ((e = prepare_async<8, 4, 4, 1>()) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_fused_async_batch<8, 2, 8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)AsyncLayout<8, 2>::BYTES)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(k_fused_async_batch<8, 4, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)AsyncLayout<8, 4>::BYTES);
+}
+
+cudaError_t launch_fused_batch(const BatchArgs& B, int total_tiles, int variant, cudaStream_t st) {
+  if (variant == 1) return launch_async_batch<8, 4, 4, 1>(B, total_tiles, st);
+  return launch_async_batch<8, 2, 8, 2>(B, total_tiles, st);
 }
 
 cudaError_t launch_fused_local(const LocalArgs& a, int fid, int variant, cudaStream_t st) {

@@ -94,6 +94,37 @@ __global__ void k_scatter(Grid g, Strips s, float* __restrict__ P1, float* __res
   }
 }
 
+// Batched multiplier update over every image of a batch (W, H multiples of 4): the
+// float4 elements of all images are numbered consecutively, image by image.
+__global__ void k_interface_batch(BatchIfaceArgs B, int total4) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total4; e += gridDim.x * blockDim.x) {
+    int lo = 0, hi = B.n_img;  // find the image: elem_base[img] <= e < elem_base[img + 1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (B.elem_base[mid] <= e) lo = mid; else hi = mid;
+    }
+    const int img = lo;
+    const LocalArgs& A = B.args[img];
+    const Strips cur = B.strips[2 * img + B.cur_set], prev = B.strips[2 * img + 1 - B.cur_set];
+    const float sigma = B.sigma[img];
+    const int q = e - B.elem_base[img];
+    const int nh4 = (A.g.NR - 1) * A.g.W / 4;
+    const bool h = q < nh4;
+    const int qq = h ? q : q - nh4;
+    const float4 cs = h ? reinterpret_cast<const float4*>(cur.SB)[qq] : reinterpret_cast<const float4*>(cur.SR)[qq];
+    const float4 ct = h ? reinterpret_cast<const float4*>(cur.ST)[qq] : reinterpret_cast<const float4*>(cur.SL)[qq];
+    const float4 ps = h ? reinterpret_cast<const float4*>(prev.SB)[qq] : reinterpret_cast<const float4*>(prev.SR)[qq];
+    const float4 pt = h ? reinterpret_cast<const float4*>(prev.ST)[qq] : reinterpret_cast<const float4*>(prev.SL)[qq];
+    float4* lp = reinterpret_cast<float4*>(const_cast<float*>(h ? A.lamh : A.lamv));
+    float4 l = lp[qq];
+    l.x = lam_step(l.x, sigma, cs.x, ps.x, ct.x, pt.x);
+    l.y = lam_step(l.y, sigma, cs.y, ps.y, ct.y, pt.y);
+    l.z = lam_step(l.z, sigma, cs.z, ps.z, ct.z, pt.z);
+    l.w = lam_step(l.w, sigma, cs.w, ps.w, ct.w, pt.w);
+    lp[qq] = l;
+  }
+}
+
 int grid_for(long long n, int block) {
   long long b = (n + block - 1) / block;
   if (b < 1) b = 1;
@@ -118,6 +149,12 @@ cudaError_t launch_interface(const Grid& g, float sigma, Strips cur, Strips prev
     k_interface_v1<<<grid_for(nh + nv, block), block, 0, st>>>(nh, nv, sigma, cur.SB, cur.ST, prev.SB, prev.ST,
                                                                 lamh, cur.SR, cur.SL, prev.SR, prev.SL, lamv);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_interface_batch(const BatchIfaceArgs& a, int total4, cudaStream_t st) {
+  if (total4 == 0) return cudaSuccess;
+  k_interface_batch<<<grid_for(total4, 256), 256, 0, st>>>(a, total4);
   return cudaGetLastError();
 }
 

@@ -154,6 +154,27 @@ class Workload:
         return f, None, clean
 
 
+def batch_workload(n_images: int = 64, seed: int = 0):
+    """The mixed batch: image i has side s in {256, 512, 1024, 2048} and aspect in
+    {1:1, 2:1 landscape, 1:2 portrait} (both drawn uniformly); even i is ROF denoising
+    (sigma 0.05, alpha 10), odd i two-phase segmentation of a noisy piecewise-constant
+    image (sigma 0.05, c1 0.2, c2 0.8, alpha 20).  Returns a list of dicts with the
+    image (float32), its shape, fidelity and parameters; image i uses seed 1000*seed+i."""
+    rng = _rng(seed)
+    out = []
+    for i in range(n_images):
+        side = int(rng.choice([256, 512, 1024, 2048]))
+        aspect = int(rng.integers(0, 3))
+        h, w = (side, side) if aspect == 0 else ((side // 2, side) if aspect == 1 else (side, side // 2))
+        shapes = max(4, (h * w) // (4096 * 4096 // 400))
+        f, clean = rof_image(h, w, shapes, 0.05, 1000 * seed + i)
+        if i % 2 == 0:
+            out.append(dict(height=h, width=w, fidelity="l2", alpha=10.0, c1=0.0, c2=0.0, f=f, clean=clean))
+        else:
+            out.append(dict(height=h, width=w, fidelity="seg", alpha=20.0, c1=0.2, c2=0.8, f=f, clean=clean))
+    return out
+
+
 WORKLOADS = {
     # ROF denoising 128x128, 2x2 subdomains of 64x64, 200 outer x 10 inner
     "rof128": Workload("rof128", 128, 128, 12, 0.05, "l2", 10.0, 2, 2, 200, 10),

@@ -16,7 +16,7 @@ def _declared_functions():
     for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(hdr).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"\b(?:int|void|const char\s*\*)\s*\**\s*(dd_tv_\w+)\s*\(", text):
+        for m in re.finditer(r"\b(?:int|void|long long|const char\s*\*)\s*\**\s*(dd_tv_\w+)\s*\(", text):
             names.add(m.group(1))
     return names
 

@@ -1,0 +1,76 @@
+"""Batched solve (many images, mixed sizes and fidelities, one launch per phase):
+every image's iterate equals, bit for bit, the iterate of a solve of that image alone
+with the same parameters, and matches the FP64 oracle within the parity tolerances."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_00682_gb300 import _lib as L
+    L.load()
+    return L
+
+
+def _images():
+    specs = [(256, 256, "l2", 10.0, 0.0, 0.0), (128, 384, "seg", 20.0, 0.2, 0.8), (384, 128, "l1", 1.5, 0.0, 0.0),
+             (128, 128, "l2", 8.0, 0.0, 0.0), (512, 256, "seg", 20.0, 0.2, 0.8)]
+    out = []
+    for k, (h, w, fid, alpha, c1, c2) in enumerate(specs):
+        f, _ = synth.rof_image(h, w, 10, 0.05, 100 + k)
+        out.append(dict(height=h, width=w, fidelity=fid, alpha=alpha, c1=c1, c2=c2, f=f))
+    return out
+
+
+def test_batch_equals_single_image_solves_bitwise():
+    L = _lib()
+    ims = _images()
+    b = L.Batch(ims, inner_iters=10)
+    fs = [torch.from_numpy(m["f"]).cuda() for m in ims]
+    b.load(fs)
+    b.iterate(13)
+    for k, m in enumerate(ims):
+        u_b = b.get_u(k, torch.empty_like(fs[k]))
+        p = L.make_params(m["height"], m["width"], m["height"] // 128, m["width"] // 128, fidelity=m["fidelity"],
+                          alpha=m["alpha"], c1=m["c1"], c2=m["c2"], inner_iters=10)
+        s = L.Solver(p)
+        s.load(fs[k])
+        s.iterate(13)
+        u_s = s.get_u(torch.empty_like(fs[k]))
+        torch.cuda.synchronize()
+        assert torch.equal(u_b, u_s), k
+        J = b.energy(k)
+        assert abs(J - s.current_energy()) <= 1e-12 * abs(J)
+    assert b.pixels() == sum(m["height"] * m["width"] for m in ims)
+
+
+def test_batch_matches_oracle():
+    L = _lib()
+    ims = _images()[1:3]   # segmentation and TV-L1
+    b = L.Batch(ims, inner_iters=10)
+    fs = [torch.from_numpy(m["f"]).cuda() for m in ims]
+    b.load(fs)
+    b.iterate(20)
+    for k, m in enumerate(ims):
+        u = b.get_u(k, torch.empty_like(fs[k])).cpu().numpy().astype(np.float64)
+        tau = 1.0 if m["fidelity"] == "seg" else 50.0
+        pr = oracle.Problem(m["height"], m["width"], m["height"] // 128, m["width"] // 128, fidelity=m["fidelity"],
+                            alpha=m["alpha"], c1=m["c1"], c2=m["c2"], tau=tau, inner=10)
+        st = oracle.dd_run(pr, m["f"].astype(np.float64), 20)
+        assert np.abs(u - st.u).max() <= 5e-4
+        Jo = oracle.energy(pr, st.u, m["f"].astype(np.float64))
+        assert abs(b.energy(k) - Jo) <= 1e-5 * abs(Jo)
+
+
+def test_batch_rejects_bad_shapes():
+    L = _lib()
+    with pytest.raises(L.DDTVError) as e:
+        L.Batch([dict(height=100, width=128, fidelity="l2", alpha=1.0)])
+    assert e.value.code == L.EINVAL
