@@ -1012,6 +1012,282 @@ __global__ void __launch_bounds__(128 * TR, MINB) k_fused_async_batch(const Batc
   }
 }
 
+__device__ __forceinline__ void cp_async4(float* dst_smem, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+// Persistent asynchronous kernel.  The arithmetic and on-chip mapping of
+// k_fused_async, but each cluster loops over subdomains t = cluster, cluster + C, ...
+// While it iterates on one subdomain, every thread prefetches the values it will own
+// in the next one into shared memory (cp.async), so state loads overlap the inner
+// loop.  The two halo mbarriers live for the whole kernel; their phases are counted
+// across subdomains (K phases each per subdomain).  A consumer re-arms the next phase
+// (arrive.expect_tx) as soon as its wait on the current one completes; every halo a
+// producer sends depends on data the consumer sent after re-arming, so bytes always
+// land in the armed phase.  No barrier separates consecutive subdomains: the initial
+// pbar1 halo row is ordinary state and is prefetched from global memory, and the
+// warps that send a CTA's halos are the ones that drain (wait for) the last halo they
+// receive, which their neighbour sends only after reading the halo they sent before,
+// so no halo buffer is overwritten while it may still be read.
+template <int R, int TR>
+struct PaLayout {
+  using F = FullLayout<R, TR>;
+  static constexpr int NT = 128 * TR;
+  static constexpr int ST = (F::FLOATS + 3) & ~3;          // staging [field][r][thread]: u, f, p1, p2
+  static constexpr int SX = ST + 4 * R * NT;               // extras [x][thread]
+  static constexpr int NX = 6 + R;                          // lamh above, P1 bottom, lamh below, lamv left[R], P2 right,
+                                                            // lamv right, initial pbar1 of the row below the band
+  static constexpr int MB = (SX + NX * NT + 1) & ~1;        // mbU, mbQ
+  static constexpr size_t BYTES = sizeof(float) * MB + 16;
+};
+
+template <int R, int TR, int CL, int FID, bool MASK>
+__device__ __forceinline__ void fused_pa_body(const LocalArgs& A, const int first, const int stride) {
+  using L = FullLayout<R, TR>;
+  using P = PaLayout<R, TR>;
+  constexpr int BW = L::BW, BAND = L::BAND, NT = P::NT;
+  static_assert(CL * BAND == 128 && CL > 1, "a cluster of CTAs covers the 128 rows of a tile");
+  extern __shared__ __align__(16) float smem[];
+  float* sU = smem + L::U;
+  float* sQ2 = smem + L::Q2;
+  float* sQ1 = smem + L::Q1;
+  float* sF = smem + L::F;
+  float* sPR = smem + L::PR;
+  float* sHR = smem + L::HR;
+  float* sCo = smem + L::CO;
+  float* stg = smem + P::ST;
+  float* stx = smem + P::SX;
+  const uint32_t mbU = smem_addr(smem + P::MB);
+  const uint32_t mbQ = mbU + 8;
+
+  const Grid g = A.g;
+  const int T = g.NR * g.NC;
+  const int rank = (int)blockIdx.x;
+  const int j = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * BW + j;
+  const int lr0 = ty * R;
+  const int i0 = rank * BAND + lr0;
+  const int W2 = g.W + g.NC;
+  const float tau = A.tau;
+  const int K = A.K;
+  const bool last_row_here = rank == CL - 1 && ty == TR - 1;
+  const bool push_down = ty == TR - 1 && rank + 1 < CL;
+  const bool push_up = ty == 0 && rank > 0;
+  const bool need_uh = ty == 0 && rank > 0;
+  const bool need_qh = ty == TR - 1 && rank + 1 < CL;
+  constexpr uint32_t kHaloBytes = 4 * BW;
+  uint32_t remote_u = 0, remote_q1 = 0, remote_mbU = 0, remote_mbQ = 0;
+  if (push_down) {
+    remote_u = map_rank(smem_addr(sU + 1 + j), rank + 1);
+    remote_mbU = map_rank(mbU, rank + 1);
+  }
+  if (push_up) {
+    remote_q1 = map_rank(smem_addr(sQ1 + TR * BW + j), rank - 1);
+    remote_mbQ = map_rank(mbQ, rank - 1);
+  }
+  if (tid == 0) {
+    mbar_init(mbU, 1);
+    mbar_init(mbQ, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int q = tid; q < 8 * min(K, L::kMaxSmemCoef); q += NT) sCo[q] = reinterpret_cast<const float*>(A.coef)[q];
+  if (rank == 0) sU[1 + j] = 0.f;  // u = 0 above every tile's first row
+  if (j == 0) sU[0] = 0.f;
+  __syncthreads();
+  // arm the first phase of each halo barrier this CTA consumes
+  if (need_uh && j == 0) mbar_arrive_expect_tx(mbU, kHaloBytes);
+  if (need_qh && j == 0) mbar_arrive_expect_tx(mbQ, kHaloBytes);
+  cluster_arrive<true>();  // barriers initialised and armed everywhere before any halo is sent
+  cluster_wait();
+
+  auto prefetch = [&](int t) {
+    const int a = t / g.NC, b = t - a * g.NC;
+    const int r0 = a * 128, c0 = b * 128, gj = c0 + j;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int gi = r0 + i0 + r;
+      cp_async4(stg + (0 * R + r) * NT + tid, A.u + (size_t)gi * g.W + gj);
+      cp_async4(stg + (1 * R + r) * NT + tid, A.f + (size_t)gi * g.W + gj);
+      cp_async4(stg + (2 * R + r) * NT + tid, A.P1 + (size_t)(gi + a) * g.W + gj);
+      cp_async4(stg + (3 * R + r) * NT + tid, A.P2 + (size_t)gi * W2 + gj + b);
+    }
+    if (i0 == 0 && a > 0) cp_async4(stx + 0 * NT + tid, A.lamh + (size_t)(a - 1) * g.W + gj);
+    if (last_row_here && a + 1 < g.NR) {
+      cp_async4(stx + 1 * NT + tid, A.P1 + (size_t)(r0 + 128 + a) * g.W + gj);
+      cp_async4(stx + 2 * NT + tid, A.lamh + (size_t)a * g.W + gj);
+    }
+    if (j == 0 && b > 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) cp_async4(stx + (3 + r) * NT + tid, A.lamv + (size_t)(b - 1) * g.H + r0 + i0 + r);
+    }
+    if (j < R && b + 1 < g.NC) {
+      const int gi = r0 + i0 + j;
+      cp_async4(stx + (3 + R) * NT + tid, A.P2 + (size_t)gi * W2 + c0 + 128 + b);
+      cp_async4(stx + (4 + R) * NT + tid, A.lamv + (size_t)b * g.H + gi);
+    }
+    if (need_qh) cp_async4(stx + (5 + R) * NT + tid, A.P1 + (size_t)(r0 + i0 + R + a) * g.W + gj);
+    cp_async_commit();
+  };
+
+  bool timed_out = false;
+  uint32_t phU = 0, phQ = 0;  // index of the next phase of mbU / mbQ this CTA waits for
+  auto wait_u = [&]() {
+    if (!mbar_wait(mbU, phU & 1)) timed_out = true;
+    ++phU;
+    if (j == 0) mbar_arrive_expect_tx(mbU, kHaloBytes);  // arm the next phase
+  };
+  auto wait_q = [&]() {
+    if (!mbar_wait(mbQ, phQ & 1)) timed_out = true;
+    ++phQ;
+    if (j == 0) mbar_arrive_expect_tx(mbQ, kHaloBytes);
+  };
+
+  float* sUr = sU + (lr0 + 1) * L::US + j + 1;
+  float* sQ2r = sQ2 + lr0 * L::QS + j;
+  const float* sFr = sF + lr0 * BW + j;
+  if (first < T) prefetch(first);
+
+  for (int t = first; t < T; t += stride) {
+    const int a = t / g.NC, b = t - a * g.NC;
+    const int r0 = a * 128, c0 = b * 128, gj = c0 + j;
+    const bool s_top = a > 0, s_bot = a + 1 < g.NR, s_lft = b > 0, s_rgt = b + 1 < g.NC;
+    const float lim_left = (j == 0 && !s_lft) ? 0.f : 1.f;
+    const float lim_top = (i0 == 0 && !s_top) ? 0.f : 1.f;
+    const bool right_lane = s_rgt && j < R;
+    float u[R], p1[R], p2[R], h1[R], h2[R], q1[R];
+    uint32_t in_d = 0;
+    float pB = 0.f, hB = 0.f;
+
+    cp_async_wait_all();
+    __syncthreads();  // staging landed; the previous subdomain's shared arrays are free
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      u[r] = stg[(0 * R + r) * NT + tid];
+      float fv = stg[(1 * R + r) * NT + tid];
+      if (FID == FID_SEG) fv = (fv - A.c1) * (fv - A.c1) - (fv - A.c2) * (fv - A.c2);
+      sF[(lr0 + r) * BW + j] = fv;
+      if (MASK && A.mask[(size_t)(r0 + i0 + r) * g.W + gj]) in_d |= 1u << r;
+      p1[r] = stg[(2 * R + r) * NT + tid];
+      p2[r] = stg[(3 * R + r) * NT + tid];
+      h1[r] = p1[r];
+      h2[r] = p2[r];
+      q1[r] = p1[r];
+      sQ2[(lr0 + r) * L::QS + j] = p2[r];
+      sU[(lr0 + r + 1) * L::US] = 0.f;
+    }
+    if (i0 == 0 && s_top) h1[0] = phat_t(p1[0], stx[0 * NT + tid], tau);
+    if (j == 0 && s_lft) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) h2[r] = phat_t(p2[r], stx[(3 + r) * NT + tid], tau);
+    }
+    if (last_row_here) {
+      if (s_bot) {
+        pB = stx[1 * NT + tid];
+        hB = phat_s(pB, stx[2 * NT + tid], tau);
+      }
+      sQ1[TR * BW + j] = pB;
+    }
+    if (need_qh) sQ1[TR * BW + j] = stx[(5 + R) * NT + tid];  // first row of the band below
+    if (j < R) {
+      float pr = 0.f, hr = 0.f;
+      if (s_rgt) {
+        pr = stx[(3 + R) * NT + tid];
+        hr = phat_s(pr, stx[(4 + R) * NT + tid], tau);
+      }
+      sPR[lr0 + j] = pr;
+      sHR[lr0 + j] = hr;
+      sQ2[(lr0 + j) * L::QS + 128] = pr;
+    }
+    sQ1[ty * BW + j] = q1[0];
+    __syncthreads();  // staging consumed by every thread
+    if (t + stride < T) prefetch(t + stride);
+
+    for (int k = 0; k < K; ++k) {
+      Coef c;
+      if (k < L::kMaxSmemCoef) {
+        const float4 ca = *reinterpret_cast<const float4*>(sCo + 8 * k);
+        const float4 cb = *reinterpret_cast<const float4*>(sCo + 8 * k + 4);
+        c = Coef{ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+      } else {
+        c = A.coef[k];
+      }
+      if (need_qh && k > 0) wait_q();  // pbar1 halo of iteration k-1
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) {
+        const int r = (rr + R - 1) % R;
+        const float below = r + 1 < R ? q1[r + 1] : sQ1[(ty + 1) * BW + j];
+        const float d = div_px(q1[r], below, sQ2r[r * L::QS], sQ2r[r * L::QS + 1]);
+        u[r] = u_update<FID>(u[r], d, sFr[r * BW], MASK && ((in_d >> r) & 1u), c);
+        sUr[r * L::US] = u[r];
+        if (rr == 0 && push_down) st_async_f32(remote_u, u[R - 1], remote_mbU);
+      }
+      __syncthreads();
+      if (need_uh) wait_u();  // u halo of iteration k
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float above = r > 0 ? u[r - 1] : sUr[-L::US];
+        p_update_lim(p1[r], q1[r], u[r] - above, h1[r], c, r == 0 ? lim_top : 1.f);
+        float q2;
+        p_update_lim(p2[r], q2, u[r] - sUr[r * L::US - 1], h2[r], c, lim_left);
+        sQ2r[r * L::QS] = q2;
+        if (r == 0) {
+          sQ1[ty * BW + j] = q1[0];
+          if (push_up) st_async_f32(remote_q1, q1[0], remote_mbQ);
+        }
+      }
+      if (last_row_here && s_bot) {
+        float qB;
+        p_update(pB, qB, -u[R - 1], hB, c);
+        sQ1[TR * BW + j] = qB;
+      }
+      if (right_lane) {
+        const int lr = lr0 + j;
+        float pr = sPR[lr], qr;
+        p_update(pr, qr, -sU[(lr + 1) * L::US + 128], sHR[lr], c);
+        sPR[lr] = pr;
+        sQ2[lr * L::QS + 128] = qr;
+      }
+      __syncthreads();
+    }
+    if (need_qh) wait_q();  // drain the last pbar1 halo (not read)
+
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int gi = r0 + i0 + r;
+      A.u[(size_t)gi * g.W + gj] = u[r];
+      A.P1[(size_t)(gi + a) * g.W + gj] = p1[r];
+      A.P2[(size_t)gi * W2 + gj + b] = p2[r];
+    }
+    if (i0 == 0 && s_top) A.out.ST[(size_t)(a - 1) * g.W + gj] = p1[0];
+    if (j == 0 && s_lft) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) A.out.SL[(size_t)(b - 1) * g.H + r0 + i0 + r] = p2[r];
+    }
+    if (last_row_here && s_bot) {
+      A.P1[(size_t)(r0 + 128 + a) * g.W + gj] = pB;
+      A.out.SB[(size_t)a * g.W + gj] = pB;
+    }
+    if (right_lane) {
+      const int gi = r0 + i0 + j;
+      const float pr = sPR[lr0 + j];
+      A.P2[(size_t)gi * W2 + c0 + 128 + b] = pr;
+      A.out.SR[(size_t)b * g.H + gi] = pr;
+    }
+  }
+  cp_async_wait_all();
+  cluster_arrive<true>();  // no CTA leaves while a neighbour may still write into it
+  cluster_wait();
+  if (timed_out) atomicOr(A.err, 1);
+}
+
+template <int R, int TR, int CL, int MINB, int FID, bool MASK>
+__global__ void __launch_bounds__(128 * TR, MINB) k_fused_pa(const LocalArgs A) {
+  fused_pa_body<R, TR, CL, FID, MASK>(A, blockIdx.y, gridDim.y);
+}
+
 struct Config {
   int BW, R, TR, CL;
   const char* name;
@@ -1026,7 +1302,7 @@ constexpr Config kConfigs[] = {
     {128, 8, 4, 4, "bw128_r8_tr4_cl4"},    // class 2, variant 1: 512 threads, 1 CTA/SM
     {128, 16, 2, 4, "bw128_r16_tr2_cl4"},  // class 2, variant 2: 256 threads, 16 rows/thread
 };
-constexpr int kNumVariants = 4;
+constexpr int kNumVariants = 6;
 
 template <int BW, int R, int TR, int CL, int FID, bool MASK>
 cudaError_t launch_one(const LocalArgs& a, cudaStream_t st) {
@@ -1130,6 +1406,85 @@ cudaError_t launch_async_batch(const BatchArgs& B, int total_tiles, cudaStream_t
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_fused_async_batch<R, TR, CL, MINB>, B);
+}
+
+// clusters of the persistent kernel resident at once, per device and instantiation
+template <int R, int TR, int CL, int MINB, int FID, bool MASK>
+int& pa_clusters(int dev) {
+  static int n[64] = {0};
+  return n[dev & 63];
+}
+
+template <int R, int TR, int CL, int MINB, int FID, bool MASK>
+cudaError_t launch_pa_one(const LocalArgs& a, cudaStream_t st) {
+  using P = PaLayout<R, TR>;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int tiles = a.g.NR * a.g.NC;
+  int nc = pa_clusters<R, TR, CL, MINB, FID, MASK>(dev);
+  if (nc <= 0 || nc > tiles) nc = tiles;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL, nc, 1);
+  cfg.blockDim = dim3(128, TR, 1);
+  cfg.dynamicSmemBytes = P::BYTES;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_fused_pa<R, TR, CL, MINB, FID, MASK>, a);
+}
+
+template <int R, int TR, int CL, int MINB>
+cudaError_t launch_pa(const LocalArgs& a, int fid, cudaStream_t st) {
+  const bool m = a.mask != nullptr;
+  switch (fid) {
+    case FID_L2: return m ? launch_pa_one<R, TR, CL, MINB, FID_L2, true>(a, st) : launch_pa_one<R, TR, CL, MINB, FID_L2, false>(a, st);
+    case FID_L1: return m ? launch_pa_one<R, TR, CL, MINB, FID_L1, true>(a, st) : launch_pa_one<R, TR, CL, MINB, FID_L1, false>(a, st);
+    default: return launch_pa_one<R, TR, CL, MINB, FID_SEG, false>(a, st);
+  }
+}
+
+// shared-memory opt-in, and how many clusters fit at once (0 disables persistence)
+template <int R, int TR, int CL, int MINB, int FID, bool MASK>
+cudaError_t prepare_pa_one() {
+  using P = PaLayout<R, TR>;
+  auto kern = k_fused_pa<R, TR, CL, MINB, FID, MASK>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::BYTES);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL, 1024, 1);
+  cfg.blockDim = dim3(128, TR, 1);
+  cfg.dynamicSmemBytes = P::BYTES;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  pa_clusters<R, TR, CL, MINB, FID, MASK>(dev) = n;
+  return cudaSuccess;
+}
+
+template <int R, int TR, int CL, int MINB>
+cudaError_t prepare_pa() {
+  cudaError_t e;
+  if ((e = prepare_pa_one<R, TR, CL, MINB, FID_L2, false>()) != cudaSuccess) return e;
+  if ((e = prepare_pa_one<R, TR, CL, MINB, FID_L2, true>()) != cudaSuccess) return e;
+  if ((e = prepare_pa_one<R, TR, CL, MINB, FID_L1, false>()) != cudaSuccess) return e;
+  if ((e = prepare_pa_one<R, TR, CL, MINB, FID_L1, true>()) != cudaSuccess) return e;
+  return prepare_pa_one<R, TR, CL, MINB, FID_SEG, false>();
 }
 
 template <int R, int TR, int CL, int MINB, int FID, bool MASK>
@@ -1243,6 +1598,8 @@ cudaError_t fused_prepare() {
   if ((e = prepare_full<8, 4, 4, 1>()) != cudaSuccess) return e;
   if ((e = prepare_async<8, 2, 8, 2>()) != cudaSuccess) return e;
   if ((e = prepare_async<8, 4, 4, 1>()) != cudaSuccess) return e;
+  if ((e = prepare_pa<8, 2, 8, 2>()) != cudaSuccess) return e;
+  if ((e = prepare_pa<8, 4, 4, 1>()) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_fused_async_batch<8, 2, 8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)AsyncLayout<8, 2>::BYTES)) != cudaSuccess)
     return e;
@@ -1260,10 +1617,12 @@ cudaError_t launch_fused_local(const LocalArgs& a, int fid, int variant, cudaStr
   const int mr = (a.g.H + a.g.NR - 1) / a.g.NR, mc = (a.g.W + a.g.NC - 1) / a.g.NC;
   if (a.g.H == 128 * a.g.NR && a.g.W == 128 * a.g.NC) {  // every tile exactly 128 x 128
     switch (variant) {
-      case 0: return launch_async<8, 2, 8, 2>(a, fid, st);  // column strips, async halos: 256 threads, 2 CTAs/SM
-      case 1: return launch_async<8, 4, 4, 1>(a, fid, st);  // column strips, async halos: 512 threads
-      case 2: return launch_full<8, 4, 4, 1>(a, fid, st);   // column strips, cluster barrier: 512 threads
+      case 0: return launch_pa<8, 2, 8, 2>(a, fid, st);     // persistent, async halos, prefetch: 256 threads
+      case 1: return launch_async<8, 2, 8, 2>(a, fid, st);  // async halos, one subdomain per cluster
+      case 2: return launch_full<8, 4, 4, 1>(a, fid, st);   // cluster barrier per half-step: 512 threads
       case 3: return launch_wr<2, 8, 8, 2>(a, fid, st);     // warp rows, per-warp mbarriers
+      case 4: return launch_pa<8, 4, 4, 1>(a, fid, st);     // persistent, async halos, prefetch: 512 threads
+      case 5: return launch_async<8, 4, 4, 1>(a, fid, st);  // async halos: 512 threads
       default: return cudaErrorInvalidValue;
     }
   }

@@ -225,9 +225,24 @@ def test_fused_variants_bitwise_identical(H, W, NR, NC):
     L = _gpu()
     f, _ = synth.rof_image(H, W, 12, 0.1, 12)
     outs = []
-    for v in range(4):
+    for v in range(6):
         _, g, _, _ = _run_gpu(f, None, 7, sub_rows=NR, sub_cols=NC, alpha=8.0, variant=v)
         outs.append(g)
     for g in outs[1:]:
         for k in ("u", "P1", "P2", "lamh", "lamv"):
             assert np.array_equal(g[k], outs[0][k]), k
+
+
+@pytest.mark.slow
+def test_full_size_tvl1_inpainting_2048():
+    """TV-L1 inpainting + impulse denoising at 2048^2, 16x16 subdomains of 128^2
+    (mask on 20 % of the pixels, 10 % salt and pepper, alpha 1.5): 3 outer
+    iterations in the benchmark's launch configuration, every pixel compared."""
+    f, mask, _ = synth.tvl1_inpaint_image(2048, 2048, 100, 0.1, 0.2, 0)
+    kw = dict(sub_rows=16, sub_cols=16, fidelity="l1", alpha=1.5, inner_iters=10)
+    _, g, _, _ = _run_gpu(f, mask, 3, **kw)
+    pr, o = _run_oracle(f, mask, 3, **kw)
+    assert np.abs(g["u"] - o.u).max() <= U_TOL
+    Jg = oracle.energy(pr, g["u"], f.astype(np.float64), mask)
+    Jo = oracle.energy(pr, o.u, f.astype(np.float64), mask)
+    assert abs(Jg - Jo) <= E_TOL * Jo
