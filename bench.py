@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched multi-image measurement")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuned time-to-accuracy")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the unrolled-adjoint measurement")
     return ap.parse_args()
 
 
@@ -169,6 +170,54 @@ def cpu_baseline(f, outer=2):
     return {"value": H * W * INNER * outer / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{outer} outer iterations (x{INNER} inner) of the 4096^2 32x32-subdomain workload, "
                       f"FP64, OpenMP over subdomains, {dt:.1f} s"}
+
+
+# Algorithmic HBM bytes per pixel and inner iteration of the reverse pass: the tape
+# recomputation (u-step 24 B, p-step 38 B) and the two reverse kernels (62 B, 54 B).
+ADJ_BYTES_PER_PX_INNER = 24 + 38 + 62 + 54
+
+
+def measure_adjoint(dev):
+    """Forward and backward time of the unrolled solver on the differentiation workload:
+    8 ROF images 1024 x 1024 (sigma 0.08, alpha 10), 8 x 8 subdomains, 100 outer x 10
+    inner iterations, checkpoints every 10, loss 1/2 ||u - g||^2."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1901_00682_gb300.autograd import UnrolledDDTV
+    B, S, N, M = 8, 1024, 100, 10
+    pairs = [synth.rof_image(S, S, 400 // 16, 0.08, 500 + b) for b in range(B)]
+    f = torch.from_numpy(np.stack([p[0] for p in pairs])).to(dev).requires_grad_(True)
+    g = torch.from_numpy(np.stack([p[1] for p in pairs])).to(dev)
+    alpha = torch.tensor(10.0, dtype=torch.float64, device=dev, requires_grad=True)
+    mod = UnrolledDDTV(S, S, 8, 8, N, checkpoint_every=M, inner_iters=INNER)
+    fw, bw = [], []
+    for rep in range(3):
+        f.grad = None
+        alpha.grad = None
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        u = mod(f, alpha)
+        loss = 0.5 * ((u - g) ** 2).sum()
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        loss.backward()
+        torch.cuda.synchronize(dev)
+        t2 = time.perf_counter()
+        if rep:  # the first repetition allocates the workspaces and captures graphs
+            fw.append((t1 - t0) * 1e3)
+            bw.append((t2 - t1) * 1e3)
+    mod.close()
+    ms_f, ms_b = min(fw), min(bw)
+    px_it = B * S * S * INNER * N
+    return {"workload": "8 ROF images 1024x1024 (sigma .08, alpha 10), 8x8 subdomains, 100 outer x 10 inner, "
+                        "checkpoint every 10, loss 1/2||u_K - g||^2, dL/df and dL/dalpha",
+            "ms_forward": ms_f, "ms_backward": ms_b, "backward_over_forward": ms_b / ms_f,
+            "backward_Mpixel_iter_per_s": px_it / (ms_b * 1e-3) / 1e6,
+            "backward_effective_hbm_gbs": px_it * ADJ_BYTES_PER_PX_INNER / (ms_b * 1e-3) / 1e9,
+            "algorithmic_bytes_per_pixel_inner": ADJ_BYTES_PER_PX_INNER,
+            "timing": "host wall clock with device synchronisation, best of 2 after one warm-up"}
 
 
 def run_reference(args):
@@ -375,6 +424,10 @@ def run_ours(args):
         bt.close()
         del fs
 
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = measure_adjoint(dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(f)
@@ -389,6 +442,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "step": "1 outer iteration (interface + fused local solves), energy every 5 steps"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "time_to_accuracy": tta, "batch": batch,
+            "adjoint": adjoint,
             "clocks": clocks.summary(), "gpu_launches": launches,
             "launches_by_phase": prof_n, "phase_ms": prof_ms,
         }

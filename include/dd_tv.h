@@ -252,6 +252,49 @@ int dd_tv_batch_energy(dd_tv_batch* b, int i, double* J_out);
 /* Total pixels of the batch (sum of H_i W_i). */
 long long dd_tv_batch_pixels(const dd_tv_batch* b);
 
+/* ---- Differentiation of the unrolled outer iterations (reverse mode).
+ * The paper does not differentiate its method.  These calls give the derivative of
+ * u_N, the iterate after N outer iterations of Algorithm 1 from the initial state of
+ * dd_tv_load (u^0 = f, 0 on D, or 1/2 for DD_TV_SEG; p~ = 0; lambda = 0), with
+ * respect to the data f and the fidelity weight alpha, for a loss L(u_N) whose
+ * gradient dL/du_N the caller supplies.  It is the exact derivative of the iteration
+ * the solver runs (float32 arithmetic), with the derivative at the kinks of the
+ * pointwise maps fixed as: projection onto [-1, 1] passes iff -1 <= t <= 1; the L1
+ * shrink passes ubar iff |ubar - f| > sigma_k alpha (else the derivative goes to f);
+ * the segmentation clamp passes iff 0 <= x <= 1.  Handles of the decomposed paths
+ * (DD_TV_PATH_FUSED, DD_TV_PATH_PLAIN) only; the full-dimension path returns
+ * DD_TV_EUNSUPPORTED.
+ *
+ * dd_tv_adjoint_forward loads f_dev / mask_dev (device, as dd_tv_load; mask nullable)
+ * and runs n_outer >= 0 outer iterations, storing the state (u, p~, lambda and the
+ * interface values of p~^{n-1}) before every checkpoint_every-th outer iteration in
+ * handle-owned device memory: ceil(n_outer / m) + m states of about
+ * 4 (3 H W + 5 (interface edges)) bytes each (m = min(checkpoint_every, n_outer)),
+ * plus the reverse pass's tape and adjoint fields (about (4 + 2) inner_iters + 60
+ * bytes per pixel), allocated on the first call and kept (and grown) until
+ * dd_tv_adjoint_release or dd_tv_destroy.  Writes u_N to u_dev (device, H x W).
+ * Asynchronous on the handle's stream.  checkpoint_every < 1 returns DD_TV_EINVAL.
+ *
+ * dd_tv_adjoint_backward reads grad_u_dev (dL/du_N, device H x W) and writes dL/df to
+ * grad_f_dev (device H x W; 0 on the inpainting domain except through the fidelity
+ * terms that do not depend on f there, i.e. exactly 0 on D) and dL/dalpha to
+ * *grad_alpha (host).  It recomputes each segment of checkpoint_every outer
+ * iterations from its checkpoint and then runs the reverse of every outer iteration
+ * of the segment, last to first.  The checkpoints stay valid, so it may be called
+ * again with another gradient; the handle's current iterate afterwards is
+ * unspecified (dd_tv_get_u / dd_tv_iterate need a new load).  Returns DD_TV_EINVAL if
+ * no dd_tv_adjoint_forward preceded it since the last load.  Synchronous (it reads
+ * the alpha derivative back).
+ *
+ * dd_tv_set_alpha changes the fidelity weight of an existing handle (same checks as
+ * dd_tv_create); the next dd_tv_adjoint_forward / dd_tv_iterate use it.
+ * dd_tv_adjoint_release frees the checkpoint, tape and adjoint memory. */
+int dd_tv_adjoint_forward(dd_tv* h, const float* f_dev, const uint8_t* mask_dev, int n_outer, int checkpoint_every,
+                          float* u_dev);
+int dd_tv_adjoint_backward(dd_tv* h, const float* grad_u_dev, float* grad_f_dev, double* grad_alpha);
+int dd_tv_adjoint_release(dd_tv* h);
+int dd_tv_set_alpha(dd_tv* h, double alpha);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,10 @@ SIGNATURES = {
     "dd_tv_batch_get_u": (_i, [_vp, _i, _vp]),
     "dd_tv_batch_energy": (_i, [_vp, _i, _DP]),
     "dd_tv_batch_pixels": (ctypes.c_longlong, [_vp]),
+    "dd_tv_adjoint_forward": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
+    "dd_tv_adjoint_backward": (_i, [_vp, _vp, _vp, _DP]),
+    "dd_tv_adjoint_release": (_i, [_vp]),
+    "dd_tv_set_alpha": (_i, [_vp, _d]),
 }
 
 _lock = threading.Lock()
@@ -283,6 +287,25 @@ class Solver:
         J, D = ctypes.c_double(), ctypes.c_double()
         check(self.lib.dd_tv_gap(self.h, ctypes.byref(J), ctypes.byref(D)), self.h)
         return J.value, D.value
+
+    def set_alpha(self, alpha: float):
+        check(self.lib.dd_tv_set_alpha(self.h, float(alpha)), self.h)
+        self.params.alpha = float(alpha)
+
+    def adjoint_forward(self, f, mask, n_outer: int, checkpoint_every: int, u_out):
+        """u_N of n_outer outer iterations from f, keeping checkpoints for the reverse pass."""
+        check(self.lib.dd_tv_adjoint_forward(self.h, _ptr(f), _ptr(mask), int(n_outer), int(checkpoint_every),
+                                             _ptr(u_out)), self.h)
+        return u_out
+
+    def adjoint_backward(self, grad_u, grad_f_out) -> float:
+        """Writes dL/df into grad_f_out and returns dL/dalpha for dL/du_N = grad_u."""
+        ga = ctypes.c_double()
+        check(self.lib.dd_tv_adjoint_backward(self.h, _ptr(grad_u), _ptr(grad_f_out), ctypes.byref(ga)), self.h)
+        return ga.value
+
+    def adjoint_release(self):
+        check(self.lib.dd_tv_adjoint_release(self.h), self.h)
 
 
 class BatchImage(ctypes.Structure):

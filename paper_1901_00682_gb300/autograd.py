@@ -1,0 +1,121 @@
+"""Differentiable unrolled solver: u_N = Phi_N(f, alpha) as a torch.autograd.Function.
+
+Phi_N is N outer iterations of Algorithm 1 from the initial state of a load (u^0 = f,
+p~ = 0, lambda = 0), computed by the CUDA library.  The backward pass is the
+library's hand-written reverse pass (dd_tv_adjoint_backward): it recomputes each
+segment of ``checkpoint_every`` outer iterations from a checkpoint kept by the
+forward pass and runs the adjoint of every outer iteration of the segment in reverse
+order, giving dL/df and dL/dalpha for the incoming dL/du_N.
+
+Every image of a batch has its own library handle and CUDA stream; the images'
+forward and backward passes are issued from a small thread pool (the ctypes calls
+release the GIL), so they run concurrently on the GPU.  Argument marshalling only:
+all arithmetic runs in the library.
+"""
+from __future__ import annotations
+
+from concurrent.futures import ThreadPoolExecutor
+
+import torch
+
+from . import _lib as L
+
+
+class UnrolledDDTV:
+    """Callable u = m(f, alpha, mask=None) with f of shape (B, H, W) or (H, W)
+    (float32, CUDA, contiguous) and alpha a float, a 0-d tensor (shared by the batch)
+    or a (B,) tensor.  Gradients flow to f and to alpha when they require them."""
+
+    def __init__(self, height, width, sub_rows, sub_cols, n_outer, checkpoint_every=10, fidelity="l2", c1=0.0,
+                 c2=0.0, inner_iters=10, path="fused", variant=0, **steps):
+        self.shape = (height, width)
+        self.n_outer = int(n_outer)
+        self.every = int(checkpoint_every)
+        self.kw = dict(sub_rows=sub_rows, sub_cols=sub_cols, fidelity=fidelity, c1=c1, c2=c2,
+                       inner_iters=inner_iters, path=path, variant=variant, **steps)
+        self._handles = []   # (Solver, torch.cuda.Stream)
+        self._pool = None
+
+    def _solvers(self, n, alpha0):
+        while len(self._handles) < n:
+            st = torch.cuda.Stream()
+            p = L.make_params(*self.shape, alpha=alpha0, outer_iters=self.n_outer, **self.kw)
+            self._handles.append((L.Solver(p, st), st))
+        if self._pool is None or self._pool._max_workers < n:
+            if self._pool is not None:
+                self._pool.shutdown()
+            self._pool = ThreadPoolExecutor(max_workers=n)
+        return self._handles[:n]
+
+    def close(self):
+        for s, _ in self._handles:
+            s.close()
+        self._handles = []
+        if self._pool is not None:
+            self._pool.shutdown()
+            self._pool = None
+
+    def __call__(self, f, alpha, mask=None):
+        squeeze = f.dim() == 2
+        if squeeze:
+            f = f.unsqueeze(0)
+            mask = None if mask is None else mask.unsqueeze(0)
+        if not isinstance(alpha, torch.Tensor):
+            alpha = torch.tensor(float(alpha), dtype=torch.float64, device=f.device)
+        u = _UnrolledFn.apply(f, alpha, mask, self)
+        return u.squeeze(0) if squeeze else u
+
+
+class _UnrolledFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, f, alpha, mask, mod):
+        if f.dtype != torch.float32 or not f.is_cuda:
+            raise TypeError("f must be a float32 CUDA tensor")
+        f = f.contiguous()
+        B = f.shape[0]
+        al = alpha.detach().reshape(-1).double().cpu().tolist()
+        if len(al) not in (1, B):
+            raise ValueError("alpha must be a scalar or have one entry per image")
+        al = al * B if len(al) == 1 else al
+        hs = mod._solvers(B, al[0])
+        m = None if mask is None else mask.to(torch.uint8).contiguous()
+        u = torch.empty_like(f)
+        cur = torch.cuda.current_stream()
+        for _, st in hs:
+            st.wait_stream(cur)
+
+        fb, ub = list(f.unbind(0)), list(u.unbind(0))
+        mb = [None] * B if m is None else list(m.unbind(0))
+
+        def fwd(b):
+            s, _ = hs[b]
+            if s.params.alpha != al[b]:
+                s.set_alpha(al[b])
+            s.adjoint_forward(fb[b], mb[b], mod.n_outer, mod.every, ub[b])
+
+        list(mod._pool.map(fwd, range(B)))
+        for _, st in hs:
+            cur.wait_stream(st)
+        ctx.mod, ctx.B, ctx.alpha_shape = mod, B, alpha.shape
+        ctx.alpha_dtype = alpha.dtype
+        return u
+
+    @staticmethod
+    def backward(ctx, gu):
+        mod, B = ctx.mod, ctx.B
+        hs = mod._handles[:B]
+        gu = gu.contiguous().float()
+        gf = torch.empty_like(gu)
+        cur = torch.cuda.current_stream()
+        for _, st in hs:
+            st.wait_stream(cur)
+        gub, gfb = list(gu.unbind(0)), list(gf.unbind(0))
+        ga = list(mod._pool.map(lambda b: hs[b][0].adjoint_backward(gub[b], gfb[b]), range(B)))
+        for _, st in hs:
+            cur.wait_stream(st)
+        g_alpha = None
+        if ctx.needs_input_grad[1]:
+            t = torch.tensor(ga, dtype=torch.float64)
+            t = t.sum() if len(ctx.alpha_shape) == 0 or ctx.alpha_shape.numel() == 1 else t
+            g_alpha = t.reshape(ctx.alpha_shape).to(dtype=ctx.alpha_dtype, device=gu.device)
+        return (gf if ctx.needs_input_grad[0] else None), g_alpha, None, None

@@ -23,6 +23,24 @@ thread_local char g_create_err[512] = {0};
 
 }  // namespace
 
+// Device memory of the reverse pass (dd_tv_adjoint_*).
+struct AdjointWork {
+  int N = 0, m = 0, nck = 0;     // outer iterations, checkpoint spacing, checkpoints
+  long long gen = -1;            // load generation the checkpoints belong to
+  size_t slot = 0;               // floats per saved state
+  int cap_ck = 0, cap_seg = 0;   // saved-state slots allocated
+  float* ck = nullptr;           // cap_ck states: the state before outer c * m
+  float* seg = nullptr;          // cap_seg states: the states of one recomputed segment
+  float* ubar = nullptr;         // tape: K x H x W
+  uint8_t* M = nullptr;          // tape: K x (n1 + n2) projection pass bits
+  float *Ph = nullptr, *Pb = nullptr;  // phat / pbar (n1 + n2 each) when the handle has none
+  float *Au = nullptr, *Ad = nullptr, *Af = nullptr;
+  double* Aal = nullptr;
+  float *AP = nullptr, *AQ = nullptr, *APh = nullptr;  // n1 + n2 each
+  float *AL = nullptr, *APp = nullptr;                 // nh + nv, 2 (nh + nv)
+  double* sum_part = nullptr;
+};
+
 struct dd_tv {
   dd_tv_params p;
   Grid g;            // decomposition grid (1 x 1 for the full-dimension path)
@@ -59,6 +77,9 @@ struct dd_tv {
   bool prof = false;
   std::vector<Mark> marks;
   long long prof_launches[3] = {0, 0, 0};
+
+  long long gen = 0;             // incremented by every load (invalidates checkpoints)
+  AdjointWork* adj = nullptr;
 };
 
 namespace {
@@ -391,7 +412,164 @@ int load_common(dd_tv* h, const float* f, const uint8_t* mask, cudaMemcpyKind ki
     CK(cudaMemcpyAsync(h->mask, mask, h->npx, kind, h->stream));
   }
   drop_graphs(h);  // the mask pointer captured in the graphs may have changed
+  ++h->gen;
   return reset_state(h);
+}
+
+// ---- reverse pass of the unrolled outer iterations (dd_tv_adjoint_*)
+
+void adj_free(AdjointWork* w) {
+  if (!w) return;
+  void* bufs[] = {w->ck, w->seg, w->ubar, w->M, w->Ph, w->Pb, w->Au, w->Ad, w->Af, w->Aal, w->AP, w->AQ, w->APh,
+                  w->AL, w->APp};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  delete w;
+}
+
+// Allocates the fixed part of the workspace once per handle and grows the saved-state
+// slots to nck checkpoints and m segment states.
+int adj_reserve(dd_tv* h, int nck, int m) {
+  if (!h->adj) {
+    AdjointWork* w = new (std::nothrow) AdjointWork();
+    if (!w) return fail(h, DD_TV_ENOMEM, "out of host memory");
+    h->adj = w;
+    const size_t K = (size_t)h->p.inner_iters, nP = h->n1 + h->n2, ne = h->nh + h->nv;
+    w->slot = h->npx + nP + 5 * ne;
+    int rc;
+    if ((rc = dalloc(h, &w->ubar, K * h->npx)) || (rc = dalloc(h, &w->M, K * nP)) ||
+        (rc = dalloc(h, &w->Au, h->npx)) || (rc = dalloc(h, &w->Ad, h->npx)) || (rc = dalloc(h, &w->Af, h->npx)) ||
+        (rc = dalloc(h, &w->Aal, h->npx)) || (rc = dalloc(h, &w->AP, nP)) || (rc = dalloc(h, &w->AQ, nP)) ||
+        (rc = dalloc(h, &w->APh, nP)) || (rc = dalloc(h, &w->AL, ne)) || (rc = dalloc(h, &w->APp, 2 * ne))) {
+      adj_free(w);
+      h->adj = nullptr;
+      return rc;
+    }
+    if (!h->Ph1 && ((rc = dalloc(h, &w->Ph, nP)) || (rc = dalloc(h, &w->Pb, nP)))) {
+      adj_free(w);
+      h->adj = nullptr;
+      return rc;
+    }
+    // inactive dofs are never written by the tape: their pass bits stay 0
+    CK(cudaMemsetAsync(w->M, 0, K * nP, h->stream));
+  }
+  AdjointWork* w = h->adj;
+  if (nck > w->cap_ck) {
+    if (w->ck) cudaFree(w->ck);
+    w->ck = nullptr;
+    w->cap_ck = 0;
+    int rc = dalloc(h, &w->ck, (size_t)nck * w->slot);
+    if (rc) return rc;
+    w->cap_ck = nck;
+  }
+  if (m > w->cap_seg) {
+    if (w->seg) cudaFree(w->seg);
+    w->seg = nullptr;
+    w->cap_seg = 0;
+    int rc = dalloc(h, &w->seg, (size_t)m * w->slot);
+    if (rc) return rc;
+    w->cap_seg = m;
+  }
+  return DD_TV_OK;
+}
+
+// saved state: [u | P1 | P2 | lamh | lamv | both strip sets]
+int state_save(dd_tv* h, float* dst) {
+  const cudaStream_t st = h->stream;
+  const auto D2D = cudaMemcpyDeviceToDevice;
+  const size_t ne = h->nh + h->nv;
+  CK(cudaMemcpyAsync(dst, h->u, h->npx * sizeof(float), D2D, st));
+  dst += h->npx;
+  CK(cudaMemcpyAsync(dst, h->P1, h->n1 * sizeof(float), D2D, st));
+  dst += h->n1;
+  CK(cudaMemcpyAsync(dst, h->P2, h->n2 * sizeof(float), D2D, st));
+  dst += h->n2;
+  if (ne) {
+    if (h->nh) CK(cudaMemcpyAsync(dst, h->lamh, h->nh * sizeof(float), D2D, st));
+    if (h->nv) CK(cudaMemcpyAsync(dst + h->nh, h->lamv, h->nv * sizeof(float), D2D, st));
+    CK(cudaMemcpyAsync(dst + ne, h->strip_mem, 4 * ne * sizeof(float), D2D, st));
+  }
+  return DD_TV_OK;
+}
+
+int state_restore(dd_tv* h, const float* src, int n) {
+  const cudaStream_t st = h->stream;
+  const auto D2D = cudaMemcpyDeviceToDevice;
+  const size_t ne = h->nh + h->nv;
+  CK(cudaMemcpyAsync(h->u, src, h->npx * sizeof(float), D2D, st));
+  src += h->npx;
+  CK(cudaMemcpyAsync(h->P1, src, h->n1 * sizeof(float), D2D, st));
+  src += h->n1;
+  CK(cudaMemcpyAsync(h->P2, src, h->n2 * sizeof(float), D2D, st));
+  src += h->n2;
+  if (ne) {
+    if (h->nh) CK(cudaMemcpyAsync(h->lamh, src, h->nh * sizeof(float), D2D, st));
+    if (h->nv) CK(cudaMemcpyAsync(h->lamv, src + h->nh, h->nv * sizeof(float), D2D, st));
+    CK(cudaMemcpyAsync(h->strip_mem, src + ne, 4 * ne * sizeof(float), D2D, st));
+  }
+  h->n = n;
+  return DD_TV_OK;
+}
+
+AdjArgs adj_args(dd_tv* h) {
+  AdjointWork* w = h->adj;
+  AdjArgs r;
+  r.g = h->g;
+  r.fid = h->fid;
+  r.c1 = (float)h->p.c1;
+  r.c2 = (float)h->p.c2;
+  r.f = h->f;
+  r.mask = h->has_mask ? h->mask : nullptr;
+  r.Au = w->Au;
+  r.Ad = w->Ad;
+  r.Af = w->Af;
+  r.Aal = w->Aal;
+  r.AP1 = w->AP;
+  r.AP2 = w->AP + h->n1;
+  r.AQ1 = w->AQ;
+  r.AQ2 = w->AQ + h->n1;
+  r.APh1 = w->APh;
+  r.APh2 = w->APh + h->n1;
+  r.ALh = w->AL;
+  r.ALv = w->AL + h->nh;
+  r.APp = Strips{w->APp, w->APp + h->nh, w->APp + 2 * h->nh, w->APp + 2 * h->nh + h->nv};
+  return r;
+}
+
+// Recomputes outer iteration n from the state in the handle's buffers (h->n = n) with
+// the plain path's kernels, recording the tape of its local solves.
+int tape_outer(dd_tv* h) {
+  AdjointWork* w = h->adj;
+  const cudaStream_t st = h->stream;
+  const int par = h->n & 1;
+  CK(launch_interface(h->g, (float)h->p.sigma, h->strips[par], h->strips[1 - par], h->lamh, h->lamv, st));
+  LocalArgs a = local_args(h, 1 - par);
+  const size_t nP = h->n1 + h->n2;
+  float* Ph1 = h->Ph1 ? h->Ph1 : w->Ph;
+  float* Ph2 = h->Ph1 ? h->Ph2 : w->Ph + h->n1;
+  float* Pb1 = h->Ph1 ? h->Pb1 : w->Pb;
+  float* Pb2 = h->Ph1 ? h->Pb2 : w->Pb + h->n1;
+  CK(launch_plain_phat(a, Ph1, Ph2, Pb1, Pb2, st));
+  for (int k = 0; k < a.K; ++k) {
+    uint8_t* Mk = w->M + (size_t)k * nP;
+    CK(launch_ustep_tape(a, Pb1, Pb2, h->coef + k, h->fid, w->ubar + (size_t)k * h->npx, st));
+    CK(launch_pstep_tape(a, Ph1, Ph2, Pb1, Pb2, h->coef + k, Mk, Mk + h->n1, st));
+  }
+  return DD_TV_OK;
+}
+
+// Reverse of outer iteration n (after tape_outer).
+int reverse_outer(dd_tv* h, const AdjArgs& r) {
+  AdjointWork* w = h->adj;
+  const cudaStream_t st = h->stream;
+  const int K = h->p.inner_iters;
+  const size_t nP = h->n1 + h->n2;
+  for (int k = K - 1; k >= 0; --k) {
+    const uint8_t* Mk = w->M + (size_t)k * nP;
+    CK(launch_adj_inner(r, h->coef + k, w->ubar + (size_t)k * h->npx, Mk, Mk + h->n1, k == K - 1, k == 0, st));
+  }
+  CK(launch_adj_interface(r, (float)h->p.sigma, (float)h->p.tau, st));
+  return DD_TV_OK;
 }
 
 }  // namespace
@@ -464,7 +642,8 @@ int dd_tv_create(dd_tv** out, const dd_tv_params* p) {
   if ((rc = dalloc(h, &h->f, h->npx)) || (rc = dalloc(h, &h->u, h->npx)) || (rc = dalloc(h, &h->P1, h->n1)) ||
       (rc = dalloc(h, &h->P2, h->n2)) || (rc = dalloc(h, &h->lamh, h->nh)) || (rc = dalloc(h, &h->lamv, h->nv)) ||
       (rc = dalloc(h, &h->strip_mem, 4 * (h->nh + h->nv))) || (rc = dalloc(h, &h->coef, sched.size())) ||
-      (rc = dalloc(h, &h->partials, (size_t)reduce_partials_count())) || (rc = dalloc(h, &h->counter, 1)) ||
+      (rc = dalloc(h, &h->partials, (size_t)std::max(reduce_partials_count(), sum_f64_partials_count()))) ||
+      (rc = dalloc(h, &h->counter, 1)) ||
       (rc = dalloc(h, &h->red_out, 2)) || (rc = dalloc(h, &h->flag, 1))) {
     std::snprintf(g_create_err, sizeof(g_create_err), "%s", h->err);
     dd_tv_destroy(h);
@@ -509,6 +688,8 @@ int dd_tv_create(dd_tv** out, const dd_tv_params* p) {
 int dd_tv_destroy(dd_tv* h) {
   if (!h) return DD_TV_OK;
   drop_graphs(h);
+  adj_free(h->adj);
+  h->adj = nullptr;
   for (auto& m : h->marks) {
     cudaEventDestroy(m.a);
     cudaEventDestroy(m.b);
@@ -663,6 +844,104 @@ int dd_tv_current_energy(dd_tv* h, double* J_out) {
 int dd_tv_set_profiling(dd_tv* h, int on) {
   if (!h) return DD_TV_EINVAL;
   h->prof = on != 0;
+  return DD_TV_OK;
+}
+
+int dd_tv_set_alpha(dd_tv* h, double alpha) {
+  if (!h) return DD_TV_EINVAL;
+  dd_tv_params q = h->p;
+  q.alpha = alpha;
+  char msg[512];
+  int rc = validate(&q, msg, sizeof(msg));
+  if (rc) return fail(h, rc, "%s", msg);
+  std::vector<Coef> sched;
+  build_schedule(q, sched);
+  // kernels and captured graphs read the schedule from device memory at run time
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(h->coef, sched.data(), sched.size() * sizeof(Coef), cudaMemcpyHostToDevice));
+  h->p = q;
+  return DD_TV_OK;
+}
+
+int dd_tv_adjoint_forward(dd_tv* h, const float* f_dev, const uint8_t* mask_dev, int n_outer, int checkpoint_every,
+                          float* u_dev) {
+  if (!h) return DD_TV_EINVAL;
+  if (h->p.path == DD_TV_PATH_FULLDIM)
+    return fail(h, DD_TV_EUNSUPPORTED, "the adjoint is defined for the decomposed paths only");
+  if (!u_dev) return fail(h, DD_TV_EINVAL, "u is NULL");
+  if (n_outer < 0) return fail(h, DD_TV_EINVAL, "n_outer must be >= 0");
+  if (checkpoint_every < 1) return fail(h, DD_TV_EINVAL, "checkpoint_every must be >= 1");
+  int rc = load_common(h, f_dev, mask_dev, cudaMemcpyDeviceToDevice);
+  if (rc) return rc;
+  const int m = std::max(1, std::min(checkpoint_every, n_outer));
+  const int nck = n_outer == 0 ? 0 : (n_outer + m - 1) / m;
+  if ((rc = adj_reserve(h, nck, m))) return rc;
+  AdjointWork* w = h->adj;
+  w->gen = -1;
+  for (int c = 0; c < nck; ++c) {
+    if ((rc = state_save(h, w->ck + (size_t)c * w->slot))) return rc;
+    if ((rc = run_outer(h, std::min(m, n_outer - c * m)))) return rc;
+  }
+  CK(cudaMemcpyAsync(u_dev, h->u, h->npx * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  w->N = n_outer;
+  w->m = m;
+  w->nck = nck;
+  w->gen = h->gen;
+  return DD_TV_OK;
+}
+
+int dd_tv_adjoint_backward(dd_tv* h, const float* grad_u_dev, float* grad_f_dev, double* grad_alpha) {
+  if (!h) return DD_TV_EINVAL;
+  if (!grad_u_dev || !grad_f_dev || !grad_alpha) return fail(h, DD_TV_EINVAL, "grad_u, grad_f and grad_alpha are required");
+  AdjointWork* w = h->adj;
+  if (!w || w->gen != h->gen) return fail(h, DD_TV_EINVAL, "no dd_tv_adjoint_forward since the last load");
+  const cudaStream_t st = h->stream;
+  const size_t nP = h->n1 + h->n2, ne = h->nh + h->nv;
+  CK(cudaMemcpyAsync(w->Au, grad_u_dev, h->npx * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(w->Af, 0, h->npx * sizeof(float), st));
+  CK(cudaMemsetAsync(w->Aal, 0, h->npx * sizeof(double), st));
+  CK(cudaMemsetAsync(w->AP, 0, nP * sizeof(float), st));
+  CK(cudaMemsetAsync(w->AQ, 0, nP * sizeof(float), st));
+  if (ne) {
+    CK(cudaMemsetAsync(w->AL, 0, ne * sizeof(float), st));
+    CK(cudaMemsetAsync(w->APp, 0, 2 * ne * sizeof(float), st));
+  }
+  const AdjArgs r = adj_args(h);
+  int rc;
+  for (int c = w->nck - 1; c >= 0; --c) {
+    const int s0 = c * w->m, e0 = std::min(s0 + w->m, w->N);
+    if ((rc = state_restore(h, w->ck + (size_t)c * w->slot, s0))) return rc;
+    for (int n = s0; n < e0; ++n) {
+      if ((rc = state_save(h, w->seg + (size_t)(n - s0) * w->slot))) return rc;
+      if (n + 1 < e0) {
+        CK(outer_once(h, n & 1));
+        h->n = n + 1;
+      }
+    }
+    for (int n = e0 - 1; n >= s0; --n) {
+      if ((rc = state_restore(h, w->seg + (size_t)(n - s0) * w->slot, n))) return rc;
+      if ((rc = tape_outer(h))) return rc;
+      if ((rc = reverse_outer(h, r))) return rc;
+    }
+  }
+  CK(launch_adj_initial(r, st));
+  CK(launch_sum_f64(w->Aal, (long long)h->npx, h->partials, h->counter, h->red_out, st));
+  CK(cudaMemcpyAsync(grad_f_dev, w->Af, h->npx * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  double ga = 0.0;
+  CK(cudaMemcpyAsync(&ga, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if ((rc = check_timeout(h))) return rc;
+  *grad_alpha = ga;
+  return DD_TV_OK;
+}
+
+int dd_tv_adjoint_release(dd_tv* h) {
+  if (!h) return DD_TV_EINVAL;
+  if (h->adj) {
+    CK(cudaStreamSynchronize(h->stream));
+    adj_free(h->adj);
+    h->adj = nullptr;
+  }
   return DD_TV_OK;
 }
 

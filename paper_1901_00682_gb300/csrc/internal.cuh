@@ -62,6 +62,23 @@ struct BatchIfaceArgs {
   int cur_set;             // strip set holding p~^n
 };
 
+// Adjoint fields of the reverse pass (kernels_adjoint.cu).  A* is the adjoint of the
+// named forward quantity; AP/AQ/APh live on the torn layout of P1/P2.
+struct AdjArgs {
+  Grid g;
+  int fid;
+  float c1, c2;
+  const float* f;          // H x W
+  const uint8_t* mask;     // H x W or nullptr
+  float *Au, *Ad, *Af;     // H x W: u, div pbar (scaled), f
+  double* Aal;             // H x W per-pixel alpha adjoint (summed at the end)
+  float *AP1, *AP2;        // p
+  float *AQ1, *AQ2;        // pbar
+  float *APh1, *APh2;      // phat
+  float *ALh, *ALv;        // lambda
+  Strips APp;              // interface values of p~^{n-1}
+};
+
 // ---- kernels_interface.cu
 // lambda += sigma ((2 cur_s - prev_s) - (2 cur_t - prev_t)) on every interface edge.
 cudaError_t launch_interface(const Grid& g, float sigma, Strips cur, Strips prev, float* lamh, float* lamv,
@@ -109,6 +126,25 @@ cudaError_t launch_energy(const Grid& g, int fidelity, float alpha, float c1, fl
                           const float* f, const uint8_t* mask, const float* P1, const float* P2, double* partials,
                           unsigned int* counter, double* out, cudaStream_t st);
 int reduce_partials_count();
+
+// ---- kernels_adjoint.cu
+// u-step / p-step of the plain path that also record ubar (H x W) and the projection's
+// pass bit of every active dof (M1 (H+NR) x W, M2 H x (W+NC); inactive dofs untouched).
+cudaError_t launch_ustep_tape(const LocalArgs& a, const float* Pb1, const float* Pb2, const Coef* ck, int fidelity,
+                              float* ubar_out, cudaStream_t st);
+cudaError_t launch_pstep_tape(const LocalArgs& a, const float* Ph1, const float* Ph2, float* Pb1, float* Pb2,
+                              const Coef* ck, uint8_t* M1, uint8_t* M2, cudaStream_t st);
+// reverse of one inner iteration (two kernels); first / last as in adj_dof
+cudaError_t launch_adj_inner(const AdjArgs& r, const Coef* ck, const float* ubar, const uint8_t* M1,
+                             const uint8_t* M2, bool first, bool last, cudaStream_t st);
+// reverse of the multiplier update and proximal centre of one outer iteration
+cudaError_t launch_adj_interface(const AdjArgs& r, float sigma, float tau, cudaStream_t st);
+// Af += du^0/df Au
+cudaError_t launch_adj_initial(const AdjArgs& r, cudaStream_t st);
+// out[0] = sum of x[0..n) (partials: sum_f64_partials_count() doubles; counter zeroed)
+cudaError_t launch_sum_f64(const double* x, long long n, double* partials, unsigned int* counter, double* out,
+                           cudaStream_t st);
+int sum_f64_partials_count();
 
 // ---- kernels_misc.cu
 // u0 = f (0 on D) for L2/L1, 1/2 for SEG

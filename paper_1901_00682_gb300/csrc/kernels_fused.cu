@@ -70,7 +70,7 @@ struct SmemLayout {
 
 // p_update with the clamp to [-lim, lim]; lim = 0 pins an inactive dof at 0
 __device__ __forceinline__ void p_update_lim(float& p, float& pbar, float du, float phat, const Coef& c, float lim) {
-  const float t = fmaf(c.pc, du, fmaf(c.pa, p, c.pb * phat));
+  const float t = p_target(p, du, phat, c);
   const float pn = fminf(fmaxf(t, -lim), lim);
   pbar = fmaf(c.th, pn - p, pn);
   p = pn;

@@ -48,10 +48,15 @@ __device__ __forceinline__ float u_update(float u, float d, float fg, bool in_d,
   return m > 0.0f ? fg + copysignf(m, v) : fg;
 }
 
+// Argument of the projection in the p-step: (tau (p + tau_k Du) + tau_k phat) / (tau + tau_k).
+__device__ __forceinline__ float p_target(float p, float du, float phat, const Coef& c) {
+  return fmaf(c.pc, du, fmaf(c.pa, p, c.pb * phat));
+}
+
 // One dof of the p-step: q = p + tau_k Du, p_new = proj_[-1,1]((tau q + tau_k phat) /
 // (tau + tau_k)), pbar = p_new + theta_k (p_new - p).
 __device__ __forceinline__ void p_update(float& p, float& pbar, float du, float phat, const Coef& c) {
-  const float t = fmaf(c.pc, du, fmaf(c.pa, p, c.pb * phat));
+  const float t = p_target(p, du, phat, c);
   const float pn = fminf(fmaxf(t, -1.0f), 1.0f);
   pbar = fmaf(c.th, pn - p, pn);
   p = pn;
