@@ -276,9 +276,8 @@ long long dd_tv_batch_pixels(const dd_tv_batch* b);
  * Asynchronous on the handle's stream.  checkpoint_every < 1 returns DD_TV_EINVAL.
  *
  * dd_tv_adjoint_backward reads grad_u_dev (dL/du_N, device H x W) and writes dL/df to
- * grad_f_dev (device H x W; 0 on the inpainting domain except through the fidelity
- * terms that do not depend on f there, i.e. exactly 0 on D) and dL/dalpha to
- * *grad_alpha (host).  It recomputes each segment of checkpoint_every outer
+ * grad_f_dev (device H x W; exactly 0 on the inpainting domain D, where nothing
+ * depends on f) and dL/dalpha to *grad_alpha (host).  It recomputes each segment of checkpoint_every outer
  * iterations from its checkpoint and then runs the reverse of every outer iteration
  * of the segment, last to first.  The checkpoints stay valid, so it may be called
  * again with another gradient; the handle's current iterate afterwards is

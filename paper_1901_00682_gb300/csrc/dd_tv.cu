@@ -38,7 +38,11 @@ struct AdjointWork {
   double* Aal = nullptr;
   float *AP = nullptr, *AQ = nullptr, *APh = nullptr;  // n1 + n2 each
   float *AL = nullptr, *APp = nullptr;                 // nh + nv, 2 (nh + nv)
-  double* sum_part = nullptr;
+  // one graph per segment (recompute + reverse of its outer iterations), valid for
+  // the (N, m, mask) they were captured with
+  std::vector<cudaGraphExec_t> graphs;
+  int g_N = -1, g_m = -1;
+  const uint8_t* g_mask = nullptr;
 };
 
 struct dd_tv {
@@ -418,8 +422,16 @@ int load_common(dd_tv* h, const float* f, const uint8_t* mask, cudaMemcpyKind ki
 
 // ---- reverse pass of the unrolled outer iterations (dd_tv_adjoint_*)
 
+void adj_drop_graphs(AdjointWork* w) {
+  for (auto& g : w->graphs)
+    if (g) cudaGraphExecDestroy(g);
+  w->graphs.clear();
+  w->g_N = w->g_m = -1;
+}
+
 void adj_free(AdjointWork* w) {
   if (!w) return;
+  adj_drop_graphs(w);
   void* bufs[] = {w->ck, w->seg, w->ubar, w->M, w->Ph, w->Pb, w->Au, w->Ad, w->Af, w->Aal, w->AP, w->AQ, w->APh,
                   w->AL, w->APp};
   for (void* b : bufs)
@@ -439,7 +451,7 @@ int adj_reserve(dd_tv* h, int nck, int m) {
     int rc;
     if ((rc = dalloc(h, &w->ubar, K * h->npx)) || (rc = dalloc(h, &w->M, K * nP)) ||
         (rc = dalloc(h, &w->Au, h->npx)) || (rc = dalloc(h, &w->Ad, h->npx)) || (rc = dalloc(h, &w->Af, h->npx)) ||
-        (rc = dalloc(h, &w->Aal, h->npx)) || (rc = dalloc(h, &w->AP, nP)) || (rc = dalloc(h, &w->AQ, nP)) ||
+        (rc = dalloc(h, &w->Aal, (size_t)adj_alpha_slots((long long)h->npx))) || (rc = dalloc(h, &w->AP, nP)) || (rc = dalloc(h, &w->AQ, nP)) ||
         (rc = dalloc(h, &w->APh, nP)) || (rc = dalloc(h, &w->AL, ne)) || (rc = dalloc(h, &w->APp, 2 * ne))) {
       adj_free(w);
       h->adj = nullptr;
@@ -454,6 +466,7 @@ int adj_reserve(dd_tv* h, int nck, int m) {
     CK(cudaMemsetAsync(w->M, 0, K * nP, h->stream));
   }
   AdjointWork* w = h->adj;
+  if (nck > w->cap_ck || m > w->cap_seg) adj_drop_graphs(w);  // they hold the slot addresses
   if (nck > w->cap_ck) {
     if (w->ck) cudaFree(w->ck);
     w->ck = nullptr;
@@ -569,6 +582,45 @@ int reverse_outer(dd_tv* h, const AdjArgs& r) {
     CK(launch_adj_inner(r, h->coef + k, w->ubar + (size_t)k * h->npx, Mk, Mk + h->n1, k == K - 1, k == 0, st));
   }
   CK(launch_adj_interface(r, (float)h->p.sigma, (float)h->p.tau, st));
+  return DD_TV_OK;
+}
+
+// Recompute segment c from its checkpoint and run the reverse of its outer iterations.
+int adj_segment(dd_tv* h, const AdjArgs& r, int c) {
+  AdjointWork* w = h->adj;
+  const int s0 = c * w->m, e0 = std::min(s0 + w->m, w->N);
+  int rc;
+  if ((rc = state_restore(h, w->ck + (size_t)c * w->slot, s0))) return rc;
+  for (int n = s0; n < e0; ++n) {
+    if ((rc = state_save(h, w->seg + (size_t)(n - s0) * w->slot))) return rc;
+    if (n + 1 < e0) {
+      CK(outer_once(h, n & 1));
+      h->n = n + 1;
+    }
+  }
+  for (int n = e0 - 1; n >= s0; --n) {
+    if ((rc = state_restore(h, w->seg + (size_t)(n - s0) * w->slot, n))) return rc;
+    if ((rc = tape_outer(h))) return rc;
+    if ((rc = reverse_outer(h, r))) return rc;
+  }
+  return DD_TV_OK;
+}
+
+int adj_capture_segment(dd_tv* h, const AdjArgs& r, int c, cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  const int rc = adj_segment(h, r, c);
+  const cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
+  if (rc || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc ? rc : fail(h, DD_TV_ECUDA, "adjoint graph capture failed: %s", cudaGetErrorString(e2));
+  }
+  const cudaError_t e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    *out = nullptr;
+    return fail(h, DD_TV_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  }
   return DD_TV_OK;
 }
 
@@ -898,8 +950,9 @@ int dd_tv_adjoint_backward(dd_tv* h, const float* grad_u_dev, float* grad_f_dev,
   const cudaStream_t st = h->stream;
   const size_t nP = h->n1 + h->n2, ne = h->nh + h->nv;
   CK(cudaMemcpyAsync(w->Au, grad_u_dev, h->npx * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  const int nal = adj_alpha_slots((long long)h->npx);
   CK(cudaMemsetAsync(w->Af, 0, h->npx * sizeof(float), st));
-  CK(cudaMemsetAsync(w->Aal, 0, h->npx * sizeof(double), st));
+  CK(cudaMemsetAsync(w->Aal, 0, nal * sizeof(double), st));
   CK(cudaMemsetAsync(w->AP, 0, nP * sizeof(float), st));
   CK(cudaMemsetAsync(w->AQ, 0, nP * sizeof(float), st));
   if (ne) {
@@ -908,24 +961,23 @@ int dd_tv_adjoint_backward(dd_tv* h, const float* grad_u_dev, float* grad_f_dev,
   }
   const AdjArgs r = adj_args(h);
   int rc;
+  if (w->g_N != w->N || w->g_m != w->m || w->g_mask != r.mask) {
+    adj_drop_graphs(w);
+    w->graphs.assign(w->nck, nullptr);
+    w->g_N = w->N;
+    w->g_m = w->m;
+    w->g_mask = r.mask;
+  }
   for (int c = w->nck - 1; c >= 0; --c) {
-    const int s0 = c * w->m, e0 = std::min(s0 + w->m, w->N);
-    if ((rc = state_restore(h, w->ck + (size_t)c * w->slot, s0))) return rc;
-    for (int n = s0; n < e0; ++n) {
-      if ((rc = state_save(h, w->seg + (size_t)(n - s0) * w->slot))) return rc;
-      if (n + 1 < e0) {
-        CK(outer_once(h, n & 1));
-        h->n = n + 1;
-      }
+    if (h->prof) {  // measurement hooks need direct launches
+      if ((rc = adj_segment(h, r, c))) return rc;
+      continue;
     }
-    for (int n = e0 - 1; n >= s0; --n) {
-      if ((rc = state_restore(h, w->seg + (size_t)(n - s0) * w->slot, n))) return rc;
-      if ((rc = tape_outer(h))) return rc;
-      if ((rc = reverse_outer(h, r))) return rc;
-    }
+    if (!w->graphs[c] && (rc = adj_capture_segment(h, r, c, &w->graphs[c]))) return rc;
+    CK(cudaGraphLaunch(w->graphs[c], st));
   }
   CK(launch_adj_initial(r, st));
-  CK(launch_sum_f64(w->Aal, (long long)h->npx, h->partials, h->counter, h->red_out, st));
+  CK(launch_sum_f64(w->Aal, nal, h->partials, h->counter, h->red_out, st));
   CK(cudaMemcpyAsync(grad_f_dev, w->Af, h->npx * sizeof(float), cudaMemcpyDeviceToDevice, st));
   double ga = 0.0;
   CK(cudaMemcpyAsync(&ga, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -71,7 +71,7 @@ struct AdjArgs {
   const float* f;          // H x W
   const uint8_t* mask;     // H x W or nullptr
   float *Au, *Ad, *Af;     // H x W: u, div pbar (scaled), f
-  double* Aal;             // H x W per-pixel alpha adjoint (summed at the end)
+  double* Aal;             // adj_alpha_slots(H W) per-block partial sums of the alpha adjoint
   float *AP1, *AP2;        // p
   float *AQ1, *AQ2;        // pbar
   float *APh1, *APh2;      // phat
@@ -145,6 +145,8 @@ cudaError_t launch_adj_initial(const AdjArgs& r, cudaStream_t st);
 cudaError_t launch_sum_f64(const double* x, long long n, double* partials, unsigned int* counter, double* out,
                            cudaStream_t st);
 int sum_f64_partials_count();
+// number of float64 partial sums the reverse u-kernel keeps for an image of npx pixels
+int adj_alpha_slots(long long npx);
 
 // ---- kernels_misc.cu
 // u0 = f (0 on D) for L2/L1, 1/2 for SEG

@@ -139,14 +139,19 @@ __device__ __forceinline__ float at_of(const uint8_t* __restrict__ M, const floa
   return M[e] ? AP[e] + opq * AQ[e] : 0.0f;
 }
 
+// Aal: one float64 partial sum of the alpha adjoint per block; every launch of a
+// handle has the same grid, so block b always adds the same pixels (deterministic).
 template <int FID, bool MASK>
-__global__ void k_adj_u(Grid g, float c1, float c2, const float* __restrict__ f, const uint8_t* __restrict__ mask,
-                        const float* __restrict__ ubar, const uint8_t* __restrict__ M1,
-                        const uint8_t* __restrict__ M2, const float* __restrict__ AP1, const float* __restrict__ AP2,
-                        const float* __restrict__ AQ1, const float* __restrict__ AQ2, float* __restrict__ Au,
-                        float* __restrict__ Ad, float* __restrict__ Af, double* __restrict__ Aal,
-                        const Coef* __restrict__ ck) {
+__global__ void __launch_bounds__(kBlock) k_adj_u(Grid g, float c1, float c2, const float* __restrict__ f,
+                                                  const uint8_t* __restrict__ mask, const float* __restrict__ ubar,
+                                                  const uint8_t* __restrict__ M1, const uint8_t* __restrict__ M2,
+                                                  const float* __restrict__ AP1, const float* __restrict__ AP2,
+                                                  const float* __restrict__ AQ1, const float* __restrict__ AQ2,
+                                                  float* __restrict__ Au, float* __restrict__ Ad,
+                                                  float* __restrict__ Af, double* __restrict__ Aal,
+                                                  const Coef* __restrict__ ck) {
   const Coef c = *ck;
+  double acc = 0.0;
   const float opq = 1.0f + c.th;
   const int W2 = g.W + g.NC;
   const long long n = (long long)g.H * g.W;
@@ -165,7 +170,17 @@ __global__ void k_adj_u(Grid g, float c1, float c2, const float* __restrict__ f,
     Au[px] = aub;
     Ad[px] = c.sig * aub;
     if (df != 0.0f) Af[px] += df * aun;
-    if (dal != 0.0f) Aal[px] += (double)dal * (double)aun;
+    acc += (double)dal * (double)aun;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  __shared__ double sw[kBlock / 32];
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) t += sw[w];
+    Aal[blockIdx.x] += t;
   }
 }
 
@@ -361,6 +376,8 @@ cudaError_t launch_adj_initial(const AdjArgs& r, cudaStream_t st) {
 }
 
 int sum_f64_partials_count() { return kSumBlocks; }
+
+int adj_alpha_slots(long long npx) { return nblocks(npx); }
 
 cudaError_t launch_sum_f64(const double* x, long long n, double* partials, unsigned int* counter, double* out,
                            cudaStream_t st) {

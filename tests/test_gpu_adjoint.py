@@ -123,6 +123,28 @@ def test_adjoint_checkpoint_spacing_and_path_do_not_change_bits(cuda_lib):
         assert ga == base[2], (every, path)
 
 
+def test_adjoint_backward_repeats_and_profiling_mode(cuda_lib):
+    """A second backward on the same checkpoints (graph replay) and a backward with the
+    measurement hooks on (direct launches) give the bits of the first one."""
+    from paper_1901_00682_gb300 import _lib as L
+    f, g, _ = _case(64, 48, "l2", 0.0, seed=6)
+    with L.Solver(L.make_params(64, 48, 2, 3)) as s:
+        fd = torch.from_numpy(f).cuda()
+        u = torch.empty_like(fd)
+        s.adjoint_forward(fd, None, 7, 3, u)
+        gu = u - torch.from_numpy(g).cuda()
+        outs = []
+        for prof in (False, False, True):
+            s.set_profiling(prof)
+            gf = torch.empty_like(fd)
+            ga = s.adjoint_backward(gu, gf)
+            outs.append((gf.cpu().numpy(), ga))
+        s.set_profiling(False)
+        s.profile_read()
+    for gf, ga in outs[1:]:
+        assert np.array_equal(gf, outs[0][0]) and ga == outs[0][1]
+
+
 def test_adjoint_zero_outer_iterations(cuda_lib):
     """N = 0: u_0 = f, so dL/df = u_0 - g and dL/dalpha = 0."""
     f, g, _ = _case(32, 32, "l2", 0.0, seed=1)
