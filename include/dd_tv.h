@@ -84,17 +84,31 @@ typedef struct {
   int variant;            /* fused path: hardware mapping of a 128 x 128 subdomain (which
                              CTA cluster shape and rows per thread), 0 = default; the
                              arithmetic and results do not depend on it              */
+  double inner_tol;       /* >= 0.  0: every local solve runs inner_iters iterations.  > 0:
+                             adaptive inner stopping (Section 5, eq. stop_inner1): a
+                             subdomain stops after the first inner iteration k with
+                             ||p^{k+1} - p^k||_2 < inner_tol ||p^{k+1}||_2 (norms over its
+                             dual dofs; p^{k+1} = 0 counts as converged), at most
+                             inner_iters iterations.  The decision is taken in float64 on
+                             float32 sums of squares.  Fused path only (the other paths
+                             return DD_TV_EUNSUPPORTED); the fused kernel then runs a
+                             cluster-wide reduction every inner iteration.           */
 } dd_tv_params;
 
 #define DD_TV_MAX_INNER 1024
 
 typedef struct {
   int outer_done;         /* outer iterations run by the call                              */
-  long long pixel_iters;  /* H * W * inner_iters * outer_done (inner work units)            */
+  long long pixel_iters;  /* inner work units: sum over outer iterations and subdomains of
+                             (subdomain pixels x inner iterations run); H * W * inner_iters
+                             * outer_done without inner_tol                              */
   double energy;          /* J(u) at exit; NaN when not evaluated                          */
   double rel_err;         /* (energy - energy_ref)/|energy_ref|; NaN when not evaluated     */
   double ms;              /* device time of the outer iterations (CUDA events)             */
   int converged;          /* 1 if outer_tol was reached                                    */
+  int inner_max;          /* most inner iterations any subdomain ran in one outer iteration
+                             of the call (the paper's "max inner iter"; = inner_iters
+                             without inner_tol)                                          */
 } dd_tv_stats;
 
 /* Fills p with the paper's experimental settings (Section 5): tau = 50,
@@ -132,6 +146,13 @@ int dd_tv_solve_device(dd_tv* h, const float* f_dev, const uint8_t* mask_dev, fl
 int dd_tv_load(dd_tv* h, const float* f_dev, const uint8_t* mask_dev);
 int dd_tv_iterate(dd_tv* h, int n_outer);
 int dd_tv_get_u(dd_tv* h, float* u_dev);
+
+/* Inner iterations run by every subdomain (row-major subdomain order, sub_rows x
+ * sub_cols ints, host memory) in the last outer iteration, and the largest count of
+ * any subdomain in any outer iteration since the last load, solve or call of this
+ * function (*max_out, nullable; the counter is then reset).  Without inner_tol
+ * every count is inner_iters (0 before the first outer iteration).  Synchronous. */
+int dd_tv_inner_counts(dd_tv* h, int* counts_host, int* max_out);
 
 /* Number of outer iterations run since the last dd_tv_load / dd_tv_set_state. */
 int dd_tv_outer_count(const dd_tv* h);

@@ -63,6 +63,7 @@ class _Params(ctypes.Structure):
 _D = ctypes.POINTER(ctypes.c_double)
 _U8 = ctypes.POINTER(ctypes.c_ubyte)
 _P = ctypes.POINTER(_Params)
+_I = ctypes.POINTER(ctypes.c_int)
 
 
 def _load():
@@ -85,6 +86,7 @@ def _load():
                 "orc_tile_grad": (v, [i, i, i, i, i, i, _D, _D, _D]),
                 "orc_local_solve": (v, [_P, i, i, i, i, i, i, _D, _U8, _D, _D, _D, _D, _D, i]),
                 "orc_dd_run": (i, [_P, _D, _U8, i, _D, _D, _D, _D, _D, _D, _D, _D]),
+                "orc_dd_run_ex": (i, [_P, _D, _U8, i, d, _I, _I, _D, _D, _D, _D, _D, _D, _D, _D, _D]),
                 "orc_cp_run": (i, [_P, _D, _U8, i, _D, _D, _D, _D, _D]),
                 "orc_rof_accel_run": (i, [_P, _D, i, _D, _D, _D, _D, _D]),
                 "orc_torn_to_global": (v, [_P, _D, _D, _D, _D]),
@@ -191,19 +193,38 @@ def dd_init(pr: Problem, f: np.ndarray, mask=None) -> DDState:
 
 
 def dd_run(pr: Problem, f: np.ndarray, n_outer: int, state: DDState | None = None, mask=None,
-           trace: bool = False) -> DDState:
-    """Runs ``n_outer`` iterations of Algorithm 1 (in place on ``state``)."""
+           trace: bool = False, inner_tol: float = 0.0, counts=None, record: bool = False) -> DDState:
+    """Runs ``n_outer`` iterations of Algorithm 1 (in place on ``state``).
+
+    inner_tol > 0: adaptive inner stopping (Section 5, eq. stop_inner1) with at most
+    ``pr.inner`` iterations.  counts: int array (n_outer, NR*NC) forcing the inner
+    iterations of every local solve.  record: keep, on the state, ``inner_counts``
+    (n_outer, NR*NC) and ``inner_res`` (n_outer, NR*NC, pr.inner; NaN past the last
+    iteration), the relative change of p of every inner iteration."""
     lib = _load()
     f64 = _f64(f)
     m = _mask(mask)
     st = state if state is not None else dd_init(pr, f64, m)
     tr = np.zeros(max(n_outer, 1)) if trace else None
     p = pr.c()
-    lib.orc_dd_run(ctypes.byref(p), _d(f64), _u8(m), n_outer, _d(st.u), _d(st.P1), _d(st.P2), _d(st.P1prev),
-                   _d(st.P2prev), _d(st.lamh), _d(st.lamv), _d(tr))
+    T = pr.NR * pr.NC
+    cin = None
+    if counts is not None:
+        cin = np.ascontiguousarray(counts, dtype=np.int32).reshape(n_outer, T)
+        if cin.min(initial=1) < 0 or cin.max(initial=0) > pr.inner:
+            raise ValueError("forced inner counts must lie in [0, inner]")
+    cout = np.zeros((max(n_outer, 1), T), dtype=np.int32) if record else None
+    res = np.full((max(n_outer, 1), T, pr.inner), np.nan) if record else None
+    ip = lambda a: None if a is None else a.ctypes.data_as(_I)
+    lib.orc_dd_run_ex(ctypes.byref(p), _d(f64), _u8(m), n_outer, float(inner_tol), ip(cin), ip(cout), _d(res),
+                      _d(st.u), _d(st.P1), _d(st.P2), _d(st.P1prev), _d(st.P2prev), _d(st.lamh), _d(st.lamv),
+                      _d(tr))
     st.n += n_outer
     if trace:
         st.energies.extend(tr[:n_outer].tolist())
+    if record:
+        st.inner_counts = cout[:n_outer]
+        st.inner_res = res[:n_outer]
     return st
 
 

@@ -283,6 +283,26 @@ void orc_tile_grad(int mr, int mc, int top, int bottom, int left, int right, con
   tile_grad(&t, u, g1, g2);
 }
 
+/* Relative change of the dual field over one inner iteration, the quantity of the
+ * inner stopping rule (Section 5, eq. stop_inner1):
+ *   ||p^{k+1} - p^k||_2 / ||p^{k+1}||_2   over the tile's active dofs;
+ * 0 when p^{k+1} = 0 (nothing left to change: the rule counts it as converged). */
+static double rel_change(const orc_tile* t, const double* p1_new, const double* p2_new, const double* p1_old,
+                         const double* p2_old) {
+  int mr = t->mr, mc = t->mc;
+  nsum dd = {0.0, 0.0}, pp = {0.0, 0.0};
+  for (int e = 0; e < (mr + 1) * mc; ++e) {
+    nsum_add(&dd, (p1_new[e] - p1_old[e]) * (p1_new[e] - p1_old[e]));
+    nsum_add(&pp, p1_new[e] * p1_new[e]);
+  }
+  for (int e = 0; e < mr * (mc + 1); ++e) {
+    nsum_add(&dd, (p2_new[e] - p2_old[e]) * (p2_new[e] - p2_old[e]));
+    nsum_add(&pp, p2_new[e] * p2_new[e]);
+  }
+  double num = nsum_get(&dd), den = nsum_get(&pp);
+  return den > 0.0 ? sqrt(num / den) : 0.0;
+}
+
 /* Local solver (Section 5, local problem eq. local): accelerated primal-dual
  * iteration (Chambolle-Pock, Algorithm 2 of their 2011 paper) on
  *   min_u max_p  -<u, div_s p> + alpha F_s(u) - G_s^*(p),
@@ -295,9 +315,14 @@ void orc_tile_grad(int mr, int mc, int top, int bottom, int left, int right, con
  *   pbar <- pnew + theta (pnew - p);  p <- pnew
  * The schedule restarts at (tau0, sigma0) and pbar = p at every call.
  * phat == NULL selects the plain single-domain step (no proximal term, used by
- * the N = 1 comparator).  f, mask, u are the tile's pixels (mr x mc). */
-static void local_solve(const orc_params* pr, const orc_tile* t, const double* f, const unsigned char* mask,
-                        double* u, double* p1, double* p2, const double* ph1, const double* ph2, int iters) {
+ * the N = 1 comparator).  f, mask, u are the tile's pixels (mr x mc).
+ * tol > 0: stop after the first iteration whose relative change of p (rel_change)
+ * is below tol, at most iters iterations (eq. stop_inner1); res (nullable, iters
+ * entries) receives the relative change of every iteration run.  Returns the number
+ * of iterations run. */
+static int local_solve(const orc_params* pr, const orc_tile* t, const double* f, const unsigned char* mask,
+                       double* u, double* p1, double* p2, const double* ph1, const double* ph2, int iters,
+                       double tol, double* res) {
   int mr = t->mr, mc = t->mc;
   int n1 = (mr + 1) * mc, n2 = mr * (mc + 1), np = mr * mc;
   double* pb1 = (double*)malloc(sizeof(double) * n1);
@@ -305,10 +330,17 @@ static void local_solve(const orc_params* pr, const orc_tile* t, const double* f
   double* d = (double*)malloc(sizeof(double) * np);
   double* g1 = (double*)malloc(sizeof(double) * n1);
   double* g2 = (double*)malloc(sizeof(double) * n2);
+  double* o1 = (tol > 0.0 || res) ? (double*)malloc(sizeof(double) * n1) : NULL;
+  double* o2 = (tol > 0.0 || res) ? (double*)malloc(sizeof(double) * n2) : NULL;
   memcpy(pb1, p1, sizeof(double) * n1);
   memcpy(pb2, p2, sizeof(double) * n2);
   double tk = pr->tau0, sk = pr->sigma0, tau = pr->tau;
+  int done = 0;
   for (int k = 0; k < iters; ++k) {
+    if (o1) {
+      memcpy(o1, p1, sizeof(double) * n1);
+      memcpy(o2, p2, sizeof(double) * n2);
+    }
     /* u-step */
     tile_div(t, pb1, pb2, d);
     for (int q = 0; q < np; ++q)
@@ -336,8 +368,15 @@ static void local_solve(const orc_params* pr, const orc_tile* t, const double* f
     }
     tk = theta * tk;
     sk = sk / theta;
+    done = k + 1;
+    if (o1) {
+      double rc = rel_change(t, p1, p2, o1, o2);
+      if (res) res[k] = rc;
+      if (tol > 0.0 && rc < tol) break;
+    }
   }
-  free(pb1); free(pb2); free(d); free(g1); free(g2);
+  free(pb1); free(pb2); free(d); free(g1); free(g2); free(o1); free(o2);
+  return done;
 }
 
 /* extract / store one tile's block of the torn arrays */
@@ -388,9 +427,27 @@ static void scatter_tile(const orc_params* pr, int a, int b, const orc_tile* t, 
  *   p~^{n-1} <- p~^n, then u^{n+1}, p~^{n+1} are the assembled local results.
  * energy_trace (nullable) receives J(u^{n+1}) after every outer iteration.
  * mask (nullable) marks the inpainting domain D (1 = in D).  Returns 0. */
+/* orc_dd_run_ex: the same with the inner count of every local solve under control:
+ *   inner_tol > 0      adaptive inner stopping (eq. stop_inner1), at most pr->inner;
+ *   counts_in != NULL  tile s of outer iteration n runs exactly counts_in[n T + s]
+ *                      iterations (T = NR NC; overrides inner_tol);
+ *   counts_out, res    (nullable) receive the iterations run, n_outer x T, and the
+ *                      relative change of p of every iteration, n_outer x T x pr->inner
+ *                      (entries past the last iteration are left untouched). */
+int orc_dd_run_ex(const orc_params* pr, const double* f, const unsigned char* mask, int n_outer, double inner_tol,
+                  const int* counts_in, int* counts_out, double* res, double* u, double* P1, double* P2,
+                  double* P1prev, double* P2prev, double* lamh, double* lamv, double* energy_trace);
+
 int orc_dd_run(const orc_params* pr, const double* f, const unsigned char* mask, int n_outer, double* u,
                double* P1, double* P2, double* P1prev, double* P2prev, double* lamh, double* lamv,
                double* energy_trace) {
+  return orc_dd_run_ex(pr, f, mask, n_outer, 0.0, NULL, NULL, NULL, u, P1, P2, P1prev, P2prev, lamh, lamv,
+                       energy_trace);
+}
+
+int orc_dd_run_ex(const orc_params* pr, const double* f, const unsigned char* mask, int n_outer, double inner_tol,
+                  const int* counts_in, int* counts_out, double* res, double* u, double* P1, double* P2,
+                  double* P1prev, double* P2prev, double* lamh, double* lamv, double* energy_trace) {
   int H = pr->H, W = pr->W, NR = pr->NR, NC = pr->NC;
   size_t n1 = (size_t)(H + NR) * W, n2 = (size_t)H * (W + NC);
   size_t nh = (size_t)(NR - 1) * W, nv = (size_t)(NC - 1) * H;
@@ -434,7 +491,12 @@ int orc_dd_run(const orc_params* pr, const double* f, const unsigned char* mask,
         for (int i = 0; i < t.mr; ++i)
           for (int j = 0; j < t.mc; ++j) lm[i * t.mc + j] = mask[(r0 + i) * W + c0 + j];
       }
-      local_solve(pr, &t, lf, lm, lu, lp1, lp2, lh1, lh2, pr->inner);
+      const size_t slot = (size_t)n * NR * NC + s;
+      const int iters = counts_in ? counts_in[slot] : pr->inner;
+      const double tol = counts_in ? 0.0 : inner_tol;
+      const int ran = local_solve(pr, &t, lf, lm, lu, lp1, lp2, lh1, lh2, iters, tol,
+                                  res ? res + slot * pr->inner : NULL);
+      if (counts_out) counts_out[slot] = ran;
       scatter_tile(pr, a, b, &t, r0, c0, u, P1, P2, lu, lp1, lp2);
       free(lu); free(lf); free(lm); free(lp1); free(lp2); free(lh1); free(lh2);
     }
@@ -449,7 +511,7 @@ void orc_local_solve(const orc_params* pr, int mr, int mc, int top, int bottom, 
                      const double* f, const unsigned char* mask, double* u, double* p1, double* p2,
                      const double* ph1, const double* ph2, int iters) {
   orc_tile t = {mr, mc, top, bottom, left, right};
-  local_solve(pr, &t, f, mask, u, p1, p2, ph1, ph2, iters);
+  local_solve(pr, &t, f, mask, u, p1, p2, ph1, ph2, iters, 0.0, NULL);
 }
 
 /* ------------------------------------------- full-dimension comparators */

@@ -32,6 +32,7 @@ class Params(ctypes.Structure):
         ("tau0", ctypes.c_double), ("sigma0", ctypes.c_double), ("gamma", ctypes.c_double),
         ("outer_tol", ctypes.c_double), ("energy_ref", ctypes.c_double),
         ("energy_every", ctypes.c_int), ("path", ctypes.c_int), ("variant", ctypes.c_int),
+        ("inner_tol", ctypes.c_double),
     ]
 
 
@@ -39,7 +40,7 @@ class Stats(ctypes.Structure):
     _fields_ = [
         ("outer_done", ctypes.c_int), ("pixel_iters", ctypes.c_longlong),
         ("energy", ctypes.c_double), ("rel_err", ctypes.c_double),
-        ("ms", ctypes.c_double), ("converged", ctypes.c_int),
+        ("ms", ctypes.c_double), ("converged", ctypes.c_int), ("inner_max", ctypes.c_int),
     ]
 
 
@@ -60,6 +61,7 @@ SIGNATURES = {
     "dd_tv_iterate": (_i, [_vp, _i]),
     "dd_tv_get_u": (_i, [_vp, _vp]),
     "dd_tv_outer_count": (_i, [_vp]),
+    "dd_tv_inner_counts": (_i, [_vp, _vp, _vp]),
     "dd_tv_get_state": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "dd_tv_set_state": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i]),
     "dd_tv_energy": (_i, [_vp, _vp, _vp, _vp, _DP]),
@@ -133,7 +135,7 @@ def default_params() -> Params:
 def make_params(height, width, sub_rows=1, sub_cols=1, fidelity=L2, alpha=10.0, c1=0.0, c2=0.0,
                 outer_iters=100, inner_iters=10, tau=None, sigma=None, tau0=10.0, sigma0=None,
                 gamma=None, outer_tol=0.0, energy_ref=math.nan, energy_every=5, path=PATH_FUSED,
-                variant=0) -> Params:
+                variant=0, inner_tol=0.0) -> Params:
     """Params with the paper's defaults (Section 5) for every unspecified step size:
     tau = 50 (1 for segmentation), sigma = 1/(2 tau), sigma0 = 1/(8 tau0),
     gamma = 1/(8 tau)."""
@@ -151,6 +153,7 @@ def make_params(height, width, sub_rows=1, sub_cols=1, fidelity=L2, alpha=10.0, 
     p.outer_tol, p.energy_ref, p.energy_every = outer_tol, energy_ref, energy_every
     p.path = {"fused": PATH_FUSED, "plain": PATH_PLAIN, "fulldim": PATH_FULLDIM}.get(path, path)
     p.variant = variant
+    p.inner_tol = inner_tol
     return p
 
 
@@ -214,6 +217,17 @@ class Solver:
 
     def outer_count(self) -> int:
         return self.lib.dd_tv_outer_count(self.h)
+
+    def inner_counts(self):
+        """(counts of the last outer iteration, sub_rows x sub_cols int array; the
+        largest count since the last load / solve / call)."""
+        import numpy as np
+        p = self.params
+        NR, NC = (1, 1) if p.path == PATH_FULLDIM else (p.sub_rows, p.sub_cols)
+        out = np.zeros((NR, NC), dtype=np.int32)
+        mx = ctypes.c_int()
+        check(self.lib.dd_tv_inner_counts(self.h, out.ctypes.data, ctypes.byref(mx)), self.h)
+        return out, mx.value
 
     def solve_host(self, f_host, mask_host=None, u_host=None):
         """dd_tv_solve on host numpy arrays; returns (u, Stats, status)."""

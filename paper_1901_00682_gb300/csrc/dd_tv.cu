@@ -38,6 +38,7 @@ struct AdjointWork {
   double* Aal = nullptr;
   float *AP = nullptr, *AQ = nullptr, *APh = nullptr;  // n1 + n2 each
   float *AL = nullptr, *APp = nullptr;                 // nh + nv, 2 (nh + nv)
+  int4 *rowtab = nullptr, *coltab = nullptr;           // H, W: tile index, first, end
   // one graph per segment (recompute + reverse of its outer iterations), valid for
   // the (N, m, mask) they were captured with
   std::vector<cudaGraphExec_t> graphs;
@@ -69,6 +70,9 @@ struct dd_tv {
   unsigned int* counter = nullptr;
   double* red_out = nullptr;
   int* flag = nullptr;
+  int* inner_used = nullptr;             // NR * NC (adaptive inner stopping)
+  int* inner_max = nullptr;              // 1
+  unsigned long long* inner_work = nullptr;  // 1
 
   cudaGraphExec_t chunk[2] = {nullptr, nullptr};  // kGraphChunk outer iterations from parity 0 / 1
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -147,6 +151,7 @@ int validate(const dd_tv_params* p, char* msg, size_t len) {
   if (p->path == DD_TV_PATH_FUSED && (p->variant < 0 || p->variant >= fused_num_variants()))
     return BAD("variant must be in [0, %d)", fused_num_variants());
   if (p->outer_tol < 0.0 || !std::isfinite(p->outer_tol)) return BAD("outer_tol must be finite and >= 0");
+  if (p->inner_tol < 0.0 || !std::isfinite(p->inner_tol)) return BAD("inner_tol must be finite and >= 0");
   if (p->outer_tol > 0.0) {
     if (!std::isfinite(p->energy_ref) || p->energy_ref == 0.0) return BAD("outer_tol needs a finite nonzero energy_ref");
     if (p->energy_every < 1) return BAD("outer_tol needs energy_every >= 1");
@@ -202,6 +207,10 @@ LocalArgs local_args(dd_tv* h, int write_set) {
   a.out = h->strips[write_set];
   a.coef = h->coef;
   a.err = h->flag;
+  a.inner_tol2 = h->p.inner_tol * h->p.inner_tol;
+  a.inner_used = h->inner_used;
+  a.inner_max = h->inner_max;
+  a.inner_work = h->inner_work;
   return a;
 }
 
@@ -324,6 +333,9 @@ int reset_state(dd_tv* h) {
     CK(cudaMemsetAsync(h->Pb1, 0, h->n1 * sizeof(float), st));
     CK(cudaMemsetAsync(h->Pb2, 0, h->n2 * sizeof(float), st));
   }
+  CK(cudaMemsetAsync(h->inner_used, 0, (size_t)h->g.NR * h->g.NC * sizeof(int), st));
+  CK(cudaMemsetAsync(h->inner_max, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(h->inner_work, 0, sizeof(unsigned long long), st));
   h->n = 0;
   h->loaded = true;
   return DD_TV_OK;
@@ -363,6 +375,11 @@ int solve_loaded(dd_tv* h, dd_tv_stats* stats, bool sync_needed) {
     stats->ms = NAN;
     stats->converged = 0;
   }
+  const bool adaptive = p.inner_tol > 0.0;
+  if (adaptive) {
+    CK(cudaMemsetAsync(h->inner_max, 0, sizeof(int), h->stream));
+    CK(cudaMemsetAsync(h->inner_work, 0, sizeof(unsigned long long), h->stream));
+  }
   CK(cudaEventRecord(h->ev0, h->stream));
   int done = 0, rc;
   bool conv = false;
@@ -392,6 +409,16 @@ int solve_loaded(dd_tv* h, dd_tv_stats* stats, bool sync_needed) {
     CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
     stats->outer_done = done;
     stats->pixel_iters = (long long)p.height * p.width * p.inner_iters * (long long)done;
+    stats->inner_max = done > 0 ? p.inner_iters : 0;
+    if (adaptive) {
+      int mx = 0;
+      unsigned long long work = 0;
+      CK(cudaMemcpyAsync(&mx, h->inner_max, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaMemcpyAsync(&work, h->inner_work, sizeof(work), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      stats->inner_max = mx;
+      stats->pixel_iters = (long long)work;
+    }
     stats->energy = J;
     stats->rel_err = std::isnan(J) ? NAN : (J - p.energy_ref) / std::fabs(p.energy_ref);
     stats->ms = ms;
@@ -433,7 +460,7 @@ void adj_free(AdjointWork* w) {
   if (!w) return;
   adj_drop_graphs(w);
   void* bufs[] = {w->ck, w->seg, w->ubar, w->M, w->Ph, w->Pb, w->Au, w->Ad, w->Af, w->Aal, w->AP, w->AQ, w->APh,
-                  w->AL, w->APp};
+                  w->AL, w->APp, w->rowtab, w->coltab};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete w;
@@ -451,7 +478,8 @@ int adj_reserve(dd_tv* h, int nck, int m) {
     int rc;
     if ((rc = dalloc(h, &w->ubar, K * h->npx)) || (rc = dalloc(h, &w->M, K * nP)) ||
         (rc = dalloc(h, &w->Au, h->npx)) || (rc = dalloc(h, &w->Ad, h->npx)) || (rc = dalloc(h, &w->Af, h->npx)) ||
-        (rc = dalloc(h, &w->Aal, (size_t)adj_alpha_slots((long long)h->npx))) || (rc = dalloc(h, &w->AP, nP)) || (rc = dalloc(h, &w->AQ, nP)) ||
+        (rc = dalloc(h, &w->Aal, (size_t)adj_alpha_slots(h->g))) || (rc = dalloc(h, &w->rowtab, h->g.H)) ||
+        (rc = dalloc(h, &w->coltab, h->g.W)) || (rc = dalloc(h, &w->AP, nP)) || (rc = dalloc(h, &w->AQ, nP)) ||
         (rc = dalloc(h, &w->APh, nP)) || (rc = dalloc(h, &w->AL, ne)) || (rc = dalloc(h, &w->APp, 2 * ne))) {
       adj_free(w);
       h->adj = nullptr;
@@ -464,6 +492,15 @@ int adj_reserve(dd_tv* h, int nck, int m) {
     }
     // inactive dofs are never written by the tape: their pass bits stay 0
     CK(cudaMemsetAsync(w->M, 0, K * nP, h->stream));
+    std::vector<int4> rt(h->g.H), ct(h->g.W);
+    for (int a = 0; a < h->g.NR; ++a)
+      for (int i = part_start(a, h->g.H, h->g.NR); i < part_start(a + 1, h->g.H, h->g.NR); ++i)
+        rt[i] = make_int4(a, part_start(a, h->g.H, h->g.NR), part_start(a + 1, h->g.H, h->g.NR), 0);
+    for (int b = 0; b < h->g.NC; ++b)
+      for (int j = part_start(b, h->g.W, h->g.NC); j < part_start(b + 1, h->g.W, h->g.NC); ++j)
+        ct[j] = make_int4(b, part_start(b, h->g.W, h->g.NC), part_start(b + 1, h->g.W, h->g.NC), 0);
+    CK(cudaMemcpy(w->rowtab, rt.data(), rt.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(w->coltab, ct.data(), ct.size() * sizeof(int4), cudaMemcpyHostToDevice));
   }
   AdjointWork* w = h->adj;
   if (nck > w->cap_ck || m > w->cap_seg) adj_drop_graphs(w);  // they hold the slot addresses
@@ -546,6 +583,8 @@ AdjArgs adj_args(dd_tv* h) {
   r.ALh = w->AL;
   r.ALv = w->AL + h->nh;
   r.APp = Strips{w->APp, w->APp + h->nh, w->APp + 2 * h->nh, w->APp + 2 * h->nh + h->nv};
+  r.rowtab = w->rowtab;
+  r.coltab = w->coltab;
   return r;
 }
 
@@ -565,8 +604,8 @@ int tape_outer(dd_tv* h) {
   CK(launch_plain_phat(a, Ph1, Ph2, Pb1, Pb2, st));
   for (int k = 0; k < a.K; ++k) {
     uint8_t* Mk = w->M + (size_t)k * nP;
-    CK(launch_ustep_tape(a, Pb1, Pb2, h->coef + k, h->fid, w->ubar + (size_t)k * h->npx, st));
-    CK(launch_pstep_tape(a, Ph1, Ph2, Pb1, Pb2, h->coef + k, Mk, Mk + h->n1, st));
+    CK(launch_ustep_tape(a, w->rowtab, w->coltab, Pb1, Pb2, h->coef + k, h->fid, w->ubar + (size_t)k * h->npx, st));
+    CK(launch_pstep_tape(a, w->rowtab, w->coltab, Ph1, Ph2, Pb1, Pb2, h->coef + k, Mk, Mk + h->n1, st));
   }
   return DD_TV_OK;
 }
@@ -646,6 +685,7 @@ void dd_tv_default_params(dd_tv_params* p) {
   p->energy_ref = NAN;
   p->energy_every = 5;
   p->path = DD_TV_PATH_FUSED;
+  p->inner_tol = 0.0;
 }
 
 int dd_tv_create(dd_tv** out, const dd_tv_params* p) {
@@ -663,6 +703,12 @@ int dd_tv_create(dd_tv** out, const dd_tv_params* p) {
   h->fid = p->fidelity;
   const bool full = p->path == DD_TV_PATH_FULLDIM;
   h->g = Grid{p->height, p->width, full ? 1 : p->sub_rows, full ? 1 : p->sub_cols};
+  if (p->inner_tol > 0.0 && p->path != DD_TV_PATH_FUSED) {
+    fail(h, DD_TV_EUNSUPPORTED, "inner_tol > 0 (adaptive inner stopping) needs the fused path");
+    std::snprintf(g_create_err, sizeof(g_create_err), "%s", h->err);
+    delete h;
+    return DD_TV_EUNSUPPORTED;
+  }
   if (p->path == DD_TV_PATH_FUSED) {
     const int mr = (h->g.H + h->g.NR - 1) / h->g.NR, mc = (h->g.W + h->g.NC - 1) / h->g.NC;
     int maxr, maxc;
@@ -695,8 +741,9 @@ int dd_tv_create(dd_tv** out, const dd_tv_params* p) {
       (rc = dalloc(h, &h->P2, h->n2)) || (rc = dalloc(h, &h->lamh, h->nh)) || (rc = dalloc(h, &h->lamv, h->nv)) ||
       (rc = dalloc(h, &h->strip_mem, 4 * (h->nh + h->nv))) || (rc = dalloc(h, &h->coef, sched.size())) ||
       (rc = dalloc(h, &h->partials, (size_t)std::max(reduce_partials_count(), sum_f64_partials_count()))) ||
-      (rc = dalloc(h, &h->counter, 1)) ||
-      (rc = dalloc(h, &h->red_out, 2)) || (rc = dalloc(h, &h->flag, 1))) {
+      (rc = dalloc(h, &h->counter, 1)) || (rc = dalloc(h, &h->red_out, 2)) || (rc = dalloc(h, &h->flag, 1)) ||
+      (rc = dalloc(h, &h->inner_used, (size_t)h->g.NR * h->g.NC)) || (rc = dalloc(h, &h->inner_max, 1)) ||
+      (rc = dalloc(h, &h->inner_work, 1))) {
     std::snprintf(g_create_err, sizeof(g_create_err), "%s", h->err);
     dd_tv_destroy(h);
     return rc;
@@ -747,7 +794,8 @@ int dd_tv_destroy(dd_tv* h) {
     cudaEventDestroy(m.b);
   }
   void* bufs[] = {h->f, h->u, h->P1, h->P2, h->lamh, h->lamv, h->mask, h->strip_mem, h->coef, h->Ph1, h->Ph2,
-                  h->Pb1, h->Pb2, h->partials, h->counter, h->red_out, h->flag};
+                  h->Pb1, h->Pb2, h->partials, h->counter, h->red_out, h->flag, h->inner_used, h->inner_max,
+                  h->inner_work};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h->ev0) cudaEventDestroy(h->ev0);
@@ -780,6 +828,25 @@ int dd_tv_iterate(dd_tv* h, int n_outer) {
 }
 
 int dd_tv_outer_count(const dd_tv* h) { return h ? h->n : -1; }
+
+int dd_tv_inner_counts(dd_tv* h, int* counts_host, int* max_out) {
+  if (!h) return DD_TV_EINVAL;
+  if (!counts_host) return fail(h, DD_TV_EINVAL, "counts is NULL");
+  const int T = h->g.NR * h->g.NC;
+  if (h->p.inner_tol > 0.0) {
+    int mx = 0;
+    CK(cudaMemcpyAsync(counts_host, h->inner_used, T * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&mx, h->inner_max, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemsetAsync(h->inner_max, 0, sizeof(int), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (max_out) *max_out = mx;
+    return DD_TV_OK;
+  }
+  const int k = h->n > 0 ? h->p.inner_iters : 0;
+  for (int t = 0; t < T; ++t) counts_host[t] = k;
+  if (max_out) *max_out = k;
+  return DD_TV_OK;
+}
 
 int dd_tv_get_u(dd_tv* h, float* u_dev) {
   if (!h) return DD_TV_EINVAL;
@@ -923,6 +990,8 @@ int dd_tv_adjoint_forward(dd_tv* h, const float* f_dev, const uint8_t* mask_dev,
   if (!u_dev) return fail(h, DD_TV_EINVAL, "u is NULL");
   if (n_outer < 0) return fail(h, DD_TV_EINVAL, "n_outer must be >= 0");
   if (checkpoint_every < 1) return fail(h, DD_TV_EINVAL, "checkpoint_every must be >= 1");
+  if (h->p.inner_tol > 0.0)
+    return fail(h, DD_TV_EUNSUPPORTED, "the adjoint needs a fixed inner iteration count (inner_tol = 0)");
   int rc = load_common(h, f_dev, mask_dev, cudaMemcpyDeviceToDevice);
   if (rc) return rc;
   const int m = std::max(1, std::min(checkpoint_every, n_outer));
@@ -950,7 +1019,7 @@ int dd_tv_adjoint_backward(dd_tv* h, const float* grad_u_dev, float* grad_f_dev,
   const cudaStream_t st = h->stream;
   const size_t nP = h->n1 + h->n2, ne = h->nh + h->nv;
   CK(cudaMemcpyAsync(w->Au, grad_u_dev, h->npx * sizeof(float), cudaMemcpyDeviceToDevice, st));
-  const int nal = adj_alpha_slots((long long)h->npx);
+  const int nal = adj_alpha_slots(h->g);
   CK(cudaMemsetAsync(w->Af, 0, h->npx * sizeof(float), st));
   CK(cudaMemsetAsync(w->Aal, 0, nal * sizeof(double), st));
   CK(cudaMemsetAsync(w->AP, 0, nP * sizeof(float), st));

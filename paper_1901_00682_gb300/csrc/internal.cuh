@@ -39,6 +39,11 @@ struct LocalArgs {
   Strips out;            // strips of p~^{n+1} (written at the end)
   const Coef* coef;      // K coefficient sets (device)
   int* err;              // set non-zero by a kernel whose bounded wait ran out
+  // adaptive inner stopping (eq. stop_inner1); inner_tol2 = 0 selects K fixed iterations
+  double inner_tol2;               // tol^2: stop once sum (dp)^2 < tol^2 sum p^2
+  int* inner_used;                 // NR * NC: inner iterations of each tile, last launch
+  int* inner_max;                  // running maximum of inner_used
+  unsigned long long* inner_work;  // running sum of tile pixels x inner iterations
 };
 
 // Batch of images solved together (every image partitioned into exact 128 x 128
@@ -71,7 +76,9 @@ struct AdjArgs {
   const float* f;          // H x W
   const uint8_t* mask;     // H x W or nullptr
   float *Au, *Ad, *Af;     // H x W: u, div pbar (scaled), f
-  double* Aal;             // adj_alpha_slots(H W) per-block partial sums of the alpha adjoint
+  double* Aal;             // adj_alpha_slots(g) per-block partial sums of the alpha adjoint
+  const int4* rowtab;      // H: (tile row, first row, end row) of every pixel row
+  const int4* coltab;      // W: (tile column, first column, end column) of every pixel column
   float *AP1, *AP2;        // p
   float *AQ1, *AQ2;        // pbar
   float *APh1, *APh2;      // phat
@@ -130,10 +137,11 @@ int reduce_partials_count();
 // ---- kernels_adjoint.cu
 // u-step / p-step of the plain path that also record ubar (H x W) and the projection's
 // pass bit of every active dof (M1 (H+NR) x W, M2 H x (W+NC); inactive dofs untouched).
-cudaError_t launch_ustep_tape(const LocalArgs& a, const float* Pb1, const float* Pb2, const Coef* ck, int fidelity,
-                              float* ubar_out, cudaStream_t st);
-cudaError_t launch_pstep_tape(const LocalArgs& a, const float* Ph1, const float* Ph2, float* Pb1, float* Pb2,
-                              const Coef* ck, uint8_t* M1, uint8_t* M2, cudaStream_t st);
+// rt / ct: the row and column tables of AdjArgs.
+cudaError_t launch_ustep_tape(const LocalArgs& a, const int4* rt, const int4* ct, const float* Pb1, const float* Pb2,
+                              const Coef* ck, int fidelity, float* ubar_out, cudaStream_t st);
+cudaError_t launch_pstep_tape(const LocalArgs& a, const int4* rt, const int4* ct, const float* Ph1, const float* Ph2,
+                              float* Pb1, float* Pb2, const Coef* ck, uint8_t* M1, uint8_t* M2, cudaStream_t st);
 // reverse of one inner iteration (two kernels); first / last as in adj_dof
 cudaError_t launch_adj_inner(const AdjArgs& r, const Coef* ck, const float* ubar, const uint8_t* M1,
                              const uint8_t* M2, bool first, bool last, cudaStream_t st);
@@ -145,8 +153,8 @@ cudaError_t launch_adj_initial(const AdjArgs& r, cudaStream_t st);
 cudaError_t launch_sum_f64(const double* x, long long n, double* partials, unsigned int* counter, double* out,
                            cudaStream_t st);
 int sum_f64_partials_count();
-// number of float64 partial sums the reverse u-kernel keeps for an image of npx pixels
-int adj_alpha_slots(long long npx);
+// number of float64 partial sums the reverse u-kernel keeps for an image grid
+int adj_alpha_slots(const Grid& g);
 
 // ---- kernels_misc.cu
 // u0 = f (0 on D) for L2/L1, 1/2 for SEG

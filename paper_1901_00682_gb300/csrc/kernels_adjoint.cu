@@ -26,6 +26,7 @@ namespace ddtv {
 namespace {
 
 constexpr int kBlock = 256;
+constexpr int kBX = 32, kBY = kBlock / kBX;  // per-pixel kernels: 32 columns x 8 rows per block
 
 int nblocks(long long n) {
   long long b = (n + kBlock - 1) / kBlock;
@@ -33,28 +34,52 @@ int nblocks(long long n) {
   return (int)(b < 1 ? 1 : b);
 }
 
+dim3 pixel_grid(const Grid& g) { return dim3((g.W + kBX - 1) / kBX, (g.H + kBY - 1) / kBY, 1); }
+
+// One thread per pixel (i, j) of a 2-D grid; the tile row / column of every pixel row
+// / column and the tile's first and end rows / columns come from small tables (x = tile
+// index, y = first, z = end), so no per-pixel division is needed.
+struct Pix {
+  int i, j, a, b, r0, r1, c0, c1;
+};
+
+__device__ __forceinline__ bool pixel_of(const Grid& g, const int4* __restrict__ rt, const int4* __restrict__ ct,
+                                         Pix& p) {
+  p.j = blockIdx.x * kBX + threadIdx.x;
+  p.i = blockIdx.y * kBY + threadIdx.y;
+  if (p.i >= g.H || p.j >= g.W) return false;
+  const int4 r = __ldg(rt + p.i), c = __ldg(ct + p.j);
+  p.a = r.x;
+  p.r0 = r.y;
+  p.r1 = r.z;
+  p.b = c.x;
+  p.c0 = c.y;
+  p.c1 = c.z;
+  return true;
+}
+
 // ---- tape: forward steps that also record what the reverse needs
 
 template <int FID, bool MASK>
-__global__ void k_ustep_tape(Grid g, float c1, float c2, const float* __restrict__ f, const uint8_t* __restrict__ mask,
-                             float* __restrict__ u, const float* __restrict__ Pb1, const float* __restrict__ Pb2,
-                             const Coef* __restrict__ ck, float* __restrict__ ubar_out) {
+__global__ void __launch_bounds__(kBlock) k_ustep_tape(Grid g, const int4* __restrict__ rt,
+                                                       const int4* __restrict__ ct, float c1, float c2,
+                                                       const float* __restrict__ f, const uint8_t* __restrict__ mask,
+                                                       float* __restrict__ u, const float* __restrict__ Pb1,
+                                                       const float* __restrict__ Pb2, const Coef* __restrict__ ck,
+                                                       float* __restrict__ ubar_out) {
+  Pix q;
+  if (!pixel_of(g, rt, ct, q)) return;
   const Coef c = *ck;
   const int W2 = g.W + g.NC;
-  const long long n = (long long)g.H * g.W;
-  for (long long px = blockIdx.x * (long long)blockDim.x + threadIdx.x; px < n;
-       px += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(px / g.W), j = (int)(px % g.W);
-    const int a = part_of(i, g.H, g.NR), b = part_of(j, g.W, g.NC);
-    const float d = div_px(Pb1[(size_t)(i + a) * g.W + j], Pb1[(size_t)(i + a + 1) * g.W + j],
-                           Pb2[(size_t)i * W2 + j + b], Pb2[(size_t)i * W2 + j + b + 1]);
-    float fv = f[px];
-    if (FID == FID_SEG) fv = (fv - c1) * (fv - c1) - (fv - c2) * (fv - c2);
-    const bool in_d = MASK && mask[px];
-    const float uo = u[px];
-    ubar_out[px] = fmaf(c.sig, d, uo);  // the value u_update forms internally
-    u[px] = u_update<FID>(uo, d, fv, in_d, c);
-  }
+  const size_t px = (size_t)q.i * g.W + q.j;
+  const size_t et = (size_t)(q.i + q.a) * g.W + q.j, el = (size_t)q.i * W2 + q.j + q.b;
+  const float d = div_px(Pb1[et], Pb1[et + g.W], Pb2[el], Pb2[el + 1]);
+  float fv = f[px];
+  if (FID == FID_SEG) fv = (fv - c1) * (fv - c1) - (fv - c2) * (fv - c2);
+  const bool in_d = MASK && mask[px];
+  const float uo = u[px];
+  ubar_out[px] = fmaf(c.sig, d, uo);  // the value u_update forms internally
+  u[px] = u_update<FID>(uo, d, fv, in_d, c);
 }
 
 __device__ __forceinline__ void p_tape_dof(float* __restrict__ P, float* __restrict__ Pb, const float* __restrict__ Ph,
@@ -70,29 +95,27 @@ __device__ __forceinline__ void p_tape_dof(float* __restrict__ P, float* __restr
 
 // p-step over the torn field (same dof ownership as the plain path) recording the
 // projection's pass bit of every active dof; inactive dofs are never written.
-__global__ void k_pstep_tape(Grid g, const float* __restrict__ u, float* __restrict__ P1, float* __restrict__ P2,
-                             const float* __restrict__ Ph1, const float* __restrict__ Ph2, float* __restrict__ Pb1,
-                             float* __restrict__ Pb2, const Coef* __restrict__ ck, uint8_t* __restrict__ M1,
-                             uint8_t* __restrict__ M2) {
+__global__ void __launch_bounds__(kBlock) k_pstep_tape(Grid g, const int4* __restrict__ rt,
+                                                       const int4* __restrict__ ct, const float* __restrict__ u,
+                                                       float* __restrict__ P1, float* __restrict__ P2,
+                                                       const float* __restrict__ Ph1, const float* __restrict__ Ph2,
+                                                       float* __restrict__ Pb1, float* __restrict__ Pb2,
+                                                       const Coef* __restrict__ ck, uint8_t* __restrict__ M1,
+                                                       uint8_t* __restrict__ M2) {
+  Pix q;
+  if (!pixel_of(g, rt, ct, q)) return;
   const Coef c = *ck;
   const int W2 = g.W + g.NC;
-  const long long n = (long long)g.H * g.W;
-  for (long long px = blockIdx.x * (long long)blockDim.x + threadIdx.x; px < n;
-       px += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(px / g.W), j = (int)(px % g.W);
-    const int a = part_of(i, g.H, g.NR), b = part_of(j, g.W, g.NC);
-    const int r0 = part_start(a, g.H, g.NR), r1 = part_start(a + 1, g.H, g.NR);
-    const int c0 = part_start(b, g.W, g.NC), c1 = part_start(b + 1, g.W, g.NC);
-    const float uc = u[px];
-    const size_t et = (size_t)(i + a) * g.W + j;
-    if (i > r0) p_tape_dof(P1, Pb1, Ph1, M1, et, uc - u[px - g.W], c);
-    else if (a > 0) p_tape_dof(P1, Pb1, Ph1, M1, et, uc, c);
-    const size_t el = (size_t)i * W2 + j + b;
-    if (j > c0) p_tape_dof(P2, Pb2, Ph2, M2, el, uc - u[px - 1], c);
-    else if (b > 0) p_tape_dof(P2, Pb2, Ph2, M2, el, uc, c);
-    if (i == r1 - 1 && a + 1 < g.NR) p_tape_dof(P1, Pb1, Ph1, M1, et + g.W, -uc, c);
-    if (j == c1 - 1 && b + 1 < g.NC) p_tape_dof(P2, Pb2, Ph2, M2, el + 1, -uc, c);
-  }
+  const size_t px = (size_t)q.i * g.W + q.j;
+  const float uc = u[px];
+  const size_t et = (size_t)(q.i + q.a) * g.W + q.j;
+  if (q.i > q.r0) p_tape_dof(P1, Pb1, Ph1, M1, et, uc - u[px - g.W], c);
+  else if (q.a > 0) p_tape_dof(P1, Pb1, Ph1, M1, et, uc, c);
+  const size_t el = (size_t)q.i * W2 + q.j + q.b;
+  if (q.j > q.c0) p_tape_dof(P2, Pb2, Ph2, M2, el, uc - u[px - 1], c);
+  else if (q.b > 0) p_tape_dof(P2, Pb2, Ph2, M2, el, uc, c);
+  if (q.i == q.r1 - 1 && q.a + 1 < g.NR) p_tape_dof(P1, Pb1, Ph1, M1, et + g.W, -uc, c);
+  if (q.j == q.c1 - 1 && q.b + 1 < g.NC) p_tape_dof(P2, Pb2, Ph2, M2, el + 1, -uc, c);
 }
 
 // ---- reverse of one inner iteration
@@ -139,10 +162,11 @@ __device__ __forceinline__ float at_of(const uint8_t* __restrict__ M, const floa
   return M[e] ? AP[e] + opq * AQ[e] : 0.0f;
 }
 
-// Aal: one float64 partial sum of the alpha adjoint per block; every launch of a
-// handle has the same grid, so block b always adds the same pixels (deterministic).
+// Aal: one float64 partial sum of the alpha adjoint per block (block b of the 2-D grid
+// always covers the same pixels, so the sums are deterministic).
 template <int FID, bool MASK>
-__global__ void __launch_bounds__(kBlock) k_adj_u(Grid g, float c1, float c2, const float* __restrict__ f,
+__global__ void __launch_bounds__(kBlock) k_adj_u(Grid g, const int4* __restrict__ rt, const int4* __restrict__ ct,
+                                                  float c1, float c2, const float* __restrict__ f,
                                                   const uint8_t* __restrict__ mask, const float* __restrict__ ubar,
                                                   const uint8_t* __restrict__ M1, const uint8_t* __restrict__ M2,
                                                   const float* __restrict__ AP1, const float* __restrict__ AP2,
@@ -152,15 +176,13 @@ __global__ void __launch_bounds__(kBlock) k_adj_u(Grid g, float c1, float c2, co
                                                   const Coef* __restrict__ ck) {
   const Coef c = *ck;
   double acc = 0.0;
-  const float opq = 1.0f + c.th;
-  const int W2 = g.W + g.NC;
-  const long long n = (long long)g.H * g.W;
-  for (long long px = blockIdx.x * (long long)blockDim.x + threadIdx.x; px < n;
-       px += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(px / g.W), j = (int)(px % g.W);
-    const int a = part_of(i, g.H, g.NR), b = part_of(j, g.W, g.NC);
-    const size_t et = (size_t)(i + a) * g.W + j, eb = et + g.W;
-    const size_t el = (size_t)i * W2 + j + b, er = el + 1;
+  Pix q;
+  if (pixel_of(g, rt, ct, q)) {
+    const float opq = 1.0f + c.th;
+    const int W2 = g.W + g.NC;
+    const size_t px = (size_t)q.i * g.W + q.j;
+    const size_t et = (size_t)(q.i + q.a) * g.W + q.j, eb = et + g.W;
+    const size_t el = (size_t)q.i * W2 + q.j + q.b, er = el + 1;
     const float dv = div_px(c.pc * at_of(M1, AP1, AQ1, et, opq), c.pc * at_of(M1, AP1, AQ1, eb, opq),
                             c.pc * at_of(M2, AP2, AQ2, el, opq), c.pc * at_of(M2, AP2, AQ2, er, opq));
     const float aun = Au[px] - dv;
@@ -170,17 +192,18 @@ __global__ void __launch_bounds__(kBlock) k_adj_u(Grid g, float c1, float c2, co
     Au[px] = aub;
     Ad[px] = c.sig * aub;
     if (df != 0.0f) Af[px] += df * aun;
-    acc += (double)dal * (double)aun;
+    acc = (double)dal * (double)aun;
   }
+  const int tid = threadIdx.y * kBX + threadIdx.x;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   __shared__ double sw[kBlock / 32];
-  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+  if ((tid & 31) == 0) sw[tid >> 5] = acc;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     double t = 0.0;
     for (int w = 0; w < kBlock / 32; ++w) t += sw[w];
-    Aal[blockIdx.x] += t;
+    Aal[blockIdx.y * gridDim.x + blockIdx.x] += t;
   }
 }
 
@@ -203,33 +226,31 @@ __device__ __forceinline__ void adj_dof(float* __restrict__ AP, float* __restric
   }
 }
 
-__global__ void k_adj_p(Grid g, const uint8_t* __restrict__ M1, const uint8_t* __restrict__ M2,
-                        const float* __restrict__ Ad, float* __restrict__ AP1, float* __restrict__ AP2,
-                        float* __restrict__ AQ1, float* __restrict__ AQ2, float* __restrict__ APh1,
-                        float* __restrict__ APh2, const Coef* __restrict__ ck, int first, int last) {
+__global__ void __launch_bounds__(kBlock) k_adj_p(Grid g, const int4* __restrict__ rt, const int4* __restrict__ ct,
+                                                  const uint8_t* __restrict__ M1, const uint8_t* __restrict__ M2,
+                                                  const float* __restrict__ Ad, float* __restrict__ AP1,
+                                                  float* __restrict__ AP2, float* __restrict__ AQ1,
+                                                  float* __restrict__ AQ2, float* __restrict__ APh1,
+                                                  float* __restrict__ APh2, const Coef* __restrict__ ck, int first,
+                                                  int last) {
+  Pix q;
+  if (!pixel_of(g, rt, ct, q)) return;
   const Coef c = *ck;
   const float opq = 1.0f + c.th;
   const bool fi = first != 0, la = last != 0;
   const int W2 = g.W + g.NC;
-  const long long n = (long long)g.H * g.W;
-  for (long long px = blockIdx.x * (long long)blockDim.x + threadIdx.x; px < n;
-       px += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(px / g.W), j = (int)(px % g.W);
-    const int a = part_of(i, g.H, g.NR), b = part_of(j, g.W, g.NC);
-    const int r0 = part_start(a, g.H, g.NR), r1 = part_start(a + 1, g.H, g.NR);
-    const int c0 = part_start(b, g.W, g.NC), c1 = part_start(b + 1, g.W, g.NC);
-    const float ad = Ad[px];
-    const size_t et = (size_t)(i + a) * g.W + j;
-    // d = div q: the dof between pixels m (above / left) and n of one tile enters
-    // d_m with + and d_n with -, so AQ = Ad_m - Ad_n (a missing pixel counts 0)
-    if (i > r0) adj_dof(AP1, AQ1, APh1, M1, et, Ad[px - g.W] - ad, c, opq, fi, la);
-    else if (a > 0) adj_dof(AP1, AQ1, APh1, M1, et, -ad, c, opq, fi, la);
-    const size_t el = (size_t)i * W2 + j + b;
-    if (j > c0) adj_dof(AP2, AQ2, APh2, M2, el, Ad[px - 1] - ad, c, opq, fi, la);
-    else if (b > 0) adj_dof(AP2, AQ2, APh2, M2, el, -ad, c, opq, fi, la);
-    if (i == r1 - 1 && a + 1 < g.NR) adj_dof(AP1, AQ1, APh1, M1, et + g.W, ad, c, opq, fi, la);
-    if (j == c1 - 1 && b + 1 < g.NC) adj_dof(AP2, AQ2, APh2, M2, el + 1, ad, c, opq, fi, la);
-  }
+  const size_t px = (size_t)q.i * g.W + q.j;
+  const float ad = Ad[px];
+  const size_t et = (size_t)(q.i + q.a) * g.W + q.j;
+  // d = div q: the dof between pixels m (above / left) and n of one tile enters
+  // d_m with + and d_n with -, so AQ = Ad_m - Ad_n (a missing pixel counts 0)
+  if (q.i > q.r0) adj_dof(AP1, AQ1, APh1, M1, et, Ad[px - g.W] - ad, c, opq, fi, la);
+  else if (q.a > 0) adj_dof(AP1, AQ1, APh1, M1, et, -ad, c, opq, fi, la);
+  const size_t el = (size_t)q.i * W2 + q.j + q.b;
+  if (q.j > q.c0) adj_dof(AP2, AQ2, APh2, M2, el, Ad[px - 1] - ad, c, opq, fi, la);
+  else if (q.b > 0) adj_dof(AP2, AQ2, APh2, M2, el, -ad, c, opq, fi, la);
+  if (q.i == q.r1 - 1 && q.a + 1 < g.NR) adj_dof(AP1, AQ1, APh1, M1, et + g.W, ad, c, opq, fi, la);
+  if (q.j == q.c1 - 1 && q.b + 1 < g.NC) adj_dof(AP2, AQ2, APh2, M2, el + 1, ad, c, opq, fi, la);
 }
 
 // ---- reverse of the interface step of outer iteration n
@@ -314,38 +335,40 @@ __global__ void __launch_bounds__(kBlock) k_sum_f64(const double* __restrict__ x
 
 }  // namespace
 
-cudaError_t launch_ustep_tape(const LocalArgs& a, const float* Pb1, const float* Pb2, const Coef* ck, int fid,
-                              float* ubar_out, cudaStream_t st) {
+cudaError_t launch_ustep_tape(const LocalArgs& a, const int4* rt, const int4* ct, const float* Pb1, const float* Pb2,
+                              const Coef* ck, int fid, float* ubar_out, cudaStream_t st) {
   const Grid& g = a.g;
-  const int nb = nblocks((long long)g.H * g.W);
+  const dim3 grid = pixel_grid(g), block(kBX, kBY);
   const bool m = a.mask != nullptr;
+#define USTEP(F, MK) \
+  k_ustep_tape<F, MK><<<grid, block, 0, st>>>(g, rt, ct, a.c1, a.c2, a.f, a.mask, a.u, Pb1, Pb2, ck, ubar_out)
   if (fid == FID_L2) {
-    if (m) k_ustep_tape<FID_L2, true><<<nb, kBlock, 0, st>>>(g, a.c1, a.c2, a.f, a.mask, a.u, Pb1, Pb2, ck, ubar_out);
-    else k_ustep_tape<FID_L2, false><<<nb, kBlock, 0, st>>>(g, a.c1, a.c2, a.f, a.mask, a.u, Pb1, Pb2, ck, ubar_out);
+    if (m) USTEP(FID_L2, true); else USTEP(FID_L2, false);
   } else if (fid == FID_L1) {
-    if (m) k_ustep_tape<FID_L1, true><<<nb, kBlock, 0, st>>>(g, a.c1, a.c2, a.f, a.mask, a.u, Pb1, Pb2, ck, ubar_out);
-    else k_ustep_tape<FID_L1, false><<<nb, kBlock, 0, st>>>(g, a.c1, a.c2, a.f, a.mask, a.u, Pb1, Pb2, ck, ubar_out);
+    if (m) USTEP(FID_L1, true); else USTEP(FID_L1, false);
   } else {
-    k_ustep_tape<FID_SEG, false><<<nb, kBlock, 0, st>>>(g, a.c1, a.c2, a.f, nullptr, a.u, Pb1, Pb2, ck, ubar_out);
+    USTEP(FID_SEG, false);
   }
+#undef USTEP
   return cudaGetLastError();
 }
 
-cudaError_t launch_pstep_tape(const LocalArgs& a, const float* Ph1, const float* Ph2, float* Pb1, float* Pb2,
-                              const Coef* ck, uint8_t* M1, uint8_t* M2, cudaStream_t st) {
+cudaError_t launch_pstep_tape(const LocalArgs& a, const int4* rt, const int4* ct, const float* Ph1, const float* Ph2,
+                              float* Pb1, float* Pb2, const Coef* ck, uint8_t* M1, uint8_t* M2, cudaStream_t st) {
   const Grid& g = a.g;
-  k_pstep_tape<<<nblocks((long long)g.H * g.W), kBlock, 0, st>>>(g, a.u, a.P1, a.P2, Ph1, Ph2, Pb1, Pb2, ck, M1, M2);
+  k_pstep_tape<<<pixel_grid(g), dim3(kBX, kBY), 0, st>>>(g, rt, ct, a.u, a.P1, a.P2, Ph1, Ph2, Pb1, Pb2, ck, M1,
+                                                          M2);
   return cudaGetLastError();
 }
 
 cudaError_t launch_adj_inner(const AdjArgs& r, const Coef* ck, const float* ubar, const uint8_t* M1,
                              const uint8_t* M2, bool first, bool last, cudaStream_t st) {
   const Grid& g = r.g;
-  const int nb = nblocks((long long)g.H * g.W);
+  const dim3 grid = pixel_grid(g), block(kBX, kBY);
   const bool m = r.mask != nullptr;
-#define ADJ_U(F, MK)                                                                                             \
-  k_adj_u<F, MK><<<nb, kBlock, 0, st>>>(g, r.c1, r.c2, r.f, r.mask, ubar, M1, M2, r.AP1, r.AP2, r.AQ1, r.AQ2, \
-                                        r.Au, r.Ad, r.Af, r.Aal, ck)
+#define ADJ_U(F, MK)                                                                                           \
+  k_adj_u<F, MK><<<grid, block, 0, st>>>(g, r.rowtab, r.coltab, r.c1, r.c2, r.f, r.mask, ubar, M1, M2, r.AP1, \
+                                         r.AP2, r.AQ1, r.AQ2, r.Au, r.Ad, r.Af, r.Aal, ck)
   if (r.fid == FID_L2) {
     if (m) ADJ_U(FID_L2, true); else ADJ_U(FID_L2, false);
   } else if (r.fid == FID_L1) {
@@ -356,8 +379,8 @@ cudaError_t launch_adj_inner(const AdjArgs& r, const Coef* ck, const float* ubar
 #undef ADJ_U
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_adj_p<<<nb, kBlock, 0, st>>>(g, M1, M2, r.Ad, r.AP1, r.AP2, r.AQ1, r.AQ2, r.APh1, r.APh2, ck, first ? 1 : 0,
-                                 last ? 1 : 0);
+  k_adj_p<<<grid, block, 0, st>>>(g, r.rowtab, r.coltab, M1, M2, r.Ad, r.AP1, r.AP2, r.AQ1, r.AQ2, r.APh1, r.APh2,
+                                  ck, first ? 1 : 0, last ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -377,7 +400,10 @@ cudaError_t launch_adj_initial(const AdjArgs& r, cudaStream_t st) {
 
 int sum_f64_partials_count() { return kSumBlocks; }
 
-int adj_alpha_slots(long long npx) { return nblocks(npx); }
+int adj_alpha_slots(const Grid& g) {
+  const dim3 d = pixel_grid(g);
+  return (int)(d.x * d.y);
+}
 
 cudaError_t launch_sum_f64(const double* x, long long n, double* partials, unsigned int* counter, double* out,
                            cudaStream_t st) {

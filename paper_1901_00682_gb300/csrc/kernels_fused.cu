@@ -41,6 +41,10 @@ __device__ __forceinline__ void st_cluster(uint32_t addr, float v) {
   asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
 
+__device__ __forceinline__ void st_cluster_f64(uint32_t addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+
 template <bool RELEASE>
 __device__ __forceinline__ void cluster_arrive() {
   if (RELEASE)
@@ -76,11 +80,20 @@ __device__ __forceinline__ void p_update_lim(float& p, float& pbar, float du, fl
   p = pn;
 }
 
-template <int BW, int R, int TR, int CL, int FID, bool MASK>
+// ADAPT: adaptive inner stopping (Section 5, eq. stop_inner1).  Every thread sums
+// (p^{k+1} - p^k)^2 and (p^{k+1})^2 over the tile dofs it owns (float32), the CTA adds
+// the threads' sums in float64 in a fixed order, every CTA stores its pair into every
+// cluster CTA's slot array through DSMEM, and after one more cluster barrier phase
+// every CTA adds the CL pairs in rank order: all CTAs of the tile take the same
+// decision.  The u-step's first cluster wait is then taken at the end of the
+// previous iteration's p-step instead.
+template <int BW, int R, int TR, int CL, int FID, bool MASK, bool ADAPT>
 __global__ void __launch_bounds__(BW* TR, (BW * TR <= 256 ? 2 : 1)) k_fused(const LocalArgs A) {
   using L = SmemLayout<BW, R, TR>;
   constexpr int BAND = L::BAND;
   extern __shared__ float smem[];
+  __shared__ double sRed[2 * CL];            // adaptive stop: per-rank (sum dp^2, sum p^2)
+  __shared__ double sWarp[2 * (BW * TR / 32)];
   float* sU = smem + L::U;
   float* sUh = smem + L::UH;
   float* sQ2 = smem + L::Q2;
@@ -192,19 +205,38 @@ __global__ void __launch_bounds__(BW* TR, (BW * TR <= 256 ? 2 : 1)) k_fused(cons
     sU[lr * L::US + j + 1] = u[r];
   };
 
+  float sd = 0.f, sp = 0.f;  // adaptive stop: this thread's sums over its tile dofs
+  auto res_add = [&](float po, float pn) {
+    const float dp = pn - po;
+    sd = fmaf(dp, dp, sd);
+    sp = fmaf(pn, pn, sp);
+  };
+
   auto p_px = [&](int r, const Coef& c) {
     const int lr = lr0 + r;
+    const bool in_tile = ADAPT && col_ok && i0 + r < mr;
     float above;
     if (r > 0) above = u[r - 1];
     else if (ty > 0) above = sU[(lr - 1) * L::US + j + 1];
     else above = sUh[j + 1];                                 // 0 above the tile's first row
+    const float o1 = p1[r], o2 = p2[r];
     p_update_lim(p1[r], q1[r], u[r] - above, h1[r], c, r == 0 ? lim_top : 1.f);
     float q2;
     p_update_lim(p2[r], q2, u[r] - sU[lr * L::US + j], h2[r], c, lim_left);
-    if (r == rb && s_bot) p_update(pB, qB, -u[r], hB, c);
+    if (in_tile) {
+      res_add(o1, p1[r]);
+      res_add(o2, p2[r]);
+    }
+    if (r == rb && s_bot) {
+      const float oB = pB;
+      p_update(pB, qB, -u[r], hB, c);
+      if (in_tile) res_add(oB, pB);
+    }
     if (j == mc - 1 && s_rgt) {
       float pr = sPR[lr], qr;
+      const float orr = pr;
       p_update(pr, qr, -u[r], sHR[lr], c);
+      if (in_tile) res_add(orr, pr);
       sPR[lr] = pr;
       sQ2[lr * L::QS + mc] = qr;
     }
@@ -212,11 +244,12 @@ __global__ void __launch_bounds__(BW* TR, (BW * TR <= 256 ? 2 : 1)) k_fused(cons
   };
 
   // ---- inner iterations
+  int k_run = A.K;
   for (int k = 0; k < A.K; ++k) {
     const float4 ca = __ldg(coef4 + 2 * k), cb = __ldg(coef4 + 2 * k + 1);
     const Coef c{ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
     // u-step: the band's last row first (the CTA below needs it)
-    if (CL > 1) cluster_wait();
+    if (CL > 1 && (!ADAPT || k == 0)) cluster_wait();
     u_px(R - 1, c);
     if (push_down) st_cluster(remote_uh, u[R - 1]);
     if (CL > 1) {
@@ -236,8 +269,61 @@ __global__ void __launch_bounds__(BW* TR, (BW * TR <= 256 ? 2 : 1)) k_fused(cons
 #pragma unroll
     for (int r = 1; r < R; ++r) p_px(r, c);
     __syncthreads();
+    if (ADAPT) {
+      // CTA sums: warps in order, then the warp partials in order (float64)
+      const int tid = ty * BW + j, lane = tid & 31, wid = tid >> 5;
+      double wd = sd, wp = sp;
+      sd = sp = 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        wd += __shfl_down_sync(0xffffffffu, wd, o);
+        wp += __shfl_down_sync(0xffffffffu, wp, o);
+      }
+      if (lane == 0) {
+        sWarp[2 * wid] = wd;
+        sWarp[2 * wid + 1] = wp;
+      }
+      __syncthreads();
+      if (CL > 1) cluster_wait();  // the p-step's cluster phase (halo rows of pbar1)
+      if (tid == 0) {
+        double td = 0.0, tp = 0.0;
+        for (int w = 0; w < BW * TR / 32; ++w) {
+          td += sWarp[2 * w];
+          tp += sWarp[2 * w + 1];
+        }
+        if (CL > 1) {
+          for (int q = 0; q < CL; ++q) {
+            st_cluster_f64(map_rank(smem_addr(sRed + 2 * rank), q), td);
+            st_cluster_f64(map_rank(smem_addr(sRed + 2 * rank + 1), q), tp);
+          }
+        } else {
+          sRed[0] = td;
+          sRed[1] = tp;
+        }
+      }
+      if (CL > 1) {
+        cluster_arrive<true>();
+        cluster_wait();
+      } else {
+        __syncthreads();
+      }
+      double td = 0.0, tp = 0.0;
+      for (int q = 0; q < CL; ++q) {
+        td += sRed[2 * q];
+        tp += sRed[2 * q + 1];
+      }
+      if (tp == 0.0 || td < A.inner_tol2 * tp) {
+        k_run = k + 1;
+        break;
+      }
+    }
   }
-  if (CL > 1) cluster_wait();  // no CTA leaves while a neighbour may still write its halo
+  if (CL > 1 && !ADAPT) cluster_wait();  // no CTA leaves while a neighbour may still write its halo
+  if (ADAPT && rank == 0 && j == 0 && ty == 0) {
+    A.inner_used[a * g.NC + b] = k_run;
+    atomicMax(A.inner_max, k_run);
+    atomicAdd(A.inner_work, (unsigned long long)mr * (unsigned long long)mc * (unsigned long long)k_run);
+  }
 
   // ---- store u^{n+1}, p~^{n+1} and the interface strips
 #pragma unroll
@@ -1304,7 +1390,7 @@ constexpr Config kConfigs[] = {
 };
 constexpr int kNumVariants = 6;
 
-template <int BW, int R, int TR, int CL, int FID, bool MASK>
+template <int BW, int R, int TR, int CL, int FID, bool MASK, bool ADAPT>
 cudaError_t launch_one(const LocalArgs& a, cudaStream_t st) {
   using L = SmemLayout<BW, R, TR>;
   // configurations above 48 KB of shared memory need the opt-in attribute, set by
@@ -1321,17 +1407,27 @@ cudaError_t launch_one(const LocalArgs& a, cudaStream_t st) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_fused<BW, R, TR, CL, FID, MASK>, a);
+  return cudaLaunchKernelEx(&cfg, k_fused<BW, R, TR, CL, FID, MASK, ADAPT>, a);
+}
+
+template <int BW, int R, int TR, int CL, bool ADAPT>
+cudaError_t launch_fid_a(const LocalArgs& a, int fid, cudaStream_t st) {
+  const bool m = a.mask != nullptr;
+  switch (fid) {
+    case FID_L2:
+      return m ? launch_one<BW, R, TR, CL, FID_L2, true, ADAPT>(a, st)
+               : launch_one<BW, R, TR, CL, FID_L2, false, ADAPT>(a, st);
+    case FID_L1:
+      return m ? launch_one<BW, R, TR, CL, FID_L1, true, ADAPT>(a, st)
+               : launch_one<BW, R, TR, CL, FID_L1, false, ADAPT>(a, st);
+    default: return launch_one<BW, R, TR, CL, FID_SEG, false, ADAPT>(a, st);
+  }
 }
 
 template <int BW, int R, int TR, int CL>
 cudaError_t launch_fid(const LocalArgs& a, int fid, cudaStream_t st) {
-  const bool m = a.mask != nullptr;
-  switch (fid) {
-    case FID_L2: return m ? launch_one<BW, R, TR, CL, FID_L2, true>(a, st) : launch_one<BW, R, TR, CL, FID_L2, false>(a, st);
-    case FID_L1: return m ? launch_one<BW, R, TR, CL, FID_L1, true>(a, st) : launch_one<BW, R, TR, CL, FID_L1, false>(a, st);
-    default: return launch_one<BW, R, TR, CL, FID_SEG, false>(a, st);
-  }
+  return a.inner_tol2 > 0.0 ? launch_fid_a<BW, R, TR, CL, true>(a, fid, st)
+                            : launch_fid_a<BW, R, TR, CL, false>(a, fid, st);
 }
 
 template <int R, int TR, int CL, int MINB, int FID, bool MASK>
@@ -1552,7 +1648,10 @@ cudaError_t prepare_full() {
 template <int BW, int R, int TR, int CL, int FID, bool MASK>
 cudaError_t prepare_one() {
   using L = SmemLayout<BW, R, TR>;
-  return cudaFuncSetAttribute(k_fused<BW, R, TR, CL, FID, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_fused<BW, R, TR, CL, FID, MASK, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_fused<BW, R, TR, CL, FID, MASK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)L::BYTES);
 }
 
@@ -1615,7 +1714,8 @@ cudaError_t launch_fused_batch(const BatchArgs& B, int total_tiles, int variant,
 cudaError_t launch_fused_local(const LocalArgs& a, int fid, int variant, cudaStream_t st) {
   // largest tile of the (ragged) partition
   const int mr = (a.g.H + a.g.NR - 1) / a.g.NR, mc = (a.g.W + a.g.NC - 1) / a.g.NC;
-  if (a.g.H == 128 * a.g.NR && a.g.W == 128 * a.g.NC) {  // every tile exactly 128 x 128
+  if (a.inner_tol2 > 0.0) variant = 0;  // adaptive stopping: the cluster-barrier kernel only
+  if (a.inner_tol2 <= 0.0 && a.g.H == 128 * a.g.NR && a.g.W == 128 * a.g.NC) {  // every tile exactly 128 x 128
     switch (variant) {
       case 0: return launch_pa<8, 2, 8, 2>(a, fid, st);     // persistent, async halos, prefetch: 256 threads
       case 1: return launch_async<8, 2, 8, 2>(a, fid, st);  // async halos, one subdomain per cluster

@@ -191,3 +191,62 @@ def test_seg_gap_certificate():
     J, d = oracle.dd_gap(pr, st, f)
     assert J - d >= -1e-10 * abs(J)
     assert J - d < 1e-6 * abs(J)
+
+
+# ---- adaptive inner stopping (Section 5, eq. stop_inner1)
+
+def test_inner_stop_rule_matches_its_definition():
+    """The oracle's adaptive count for one tile equals the first k with
+    ||p^k - p^{k-1}||_2 < tol ||p^k||_2, recomputed here with numpy from k-iteration
+    local solves started from the same state (the schedule restarts at every call)."""
+    H = W = 24
+    f, _ = synth.rof_image(H, W, 4, 0.05, 2)
+    pr = oracle.Problem(H, W, 2, 2, alpha=10.0, inner=60)
+    st = oracle.dd_run(pr, f, 3)                       # a warm state with nonzero interfaces
+    st2 = oracle.dd_run(pr, f, 1, state=st.copy(), inner_tol=2e-3, record=True)
+    # tile (0, 0): rows 0..11, cols 0..11; its proximal centre from the state's multipliers
+    lamh = st.lamh + pr.c().sigma * (2 * oracle.jump(pr, st.P1, st.P2)[0] - oracle.jump(pr, st.P1prev, st.P2prev)[0])
+    lamv = st.lamv + pr.c().sigma * (2 * oracle.jump(pr, st.P1, st.P2)[1] - oracle.jump(pr, st.P1prev, st.P2prev)[1])
+    B1, B2 = oracle.jump_adjoint(pr, lamh, lamv)
+    Ph1, Ph2 = st.P1 - pr.tau * B1, st.P2 - pr.tau * B2
+    u0 = np.ascontiguousarray(st.u[:12, :12])
+    p10, p20 = np.ascontiguousarray(st.P1[0:13, :12]), np.ascontiguousarray(st.P2[:12, 0:13])
+    h1, h2 = np.ascontiguousarray(Ph1[0:13, :12]), np.ascontiguousarray(Ph2[:12, 0:13])
+    fl = np.ascontiguousarray(f[:12, :12], dtype=np.float64)
+    prev = (p10, p20)
+    first = None
+    for k in range(1, 61):
+        u, q1, q2 = u0.copy(), p10.copy(), p20.copy()
+        oracle.local_solve(pr, fl, u, q1, q2, h1, h2, k, sides=(0, 1, 0, 1))
+        num = np.sqrt(((q1 - prev[0]) ** 2).sum() + ((q2 - prev[1]) ** 2).sum())
+        den = np.sqrt((q1 ** 2).sum() + (q2 ** 2).sum())
+        if num < 2e-3 * den:
+            first = k
+            break
+        prev = (q1, q2)
+    assert first is not None and 1 < first < 60
+    assert st2.inner_counts[0, 0] == first
+    assert np.all(st2.inner_counts <= 60) and np.all(st2.inner_counts >= 1)
+
+
+def test_inner_stop_constant_image_single_domain():
+    """One subdomain, constant f: D u = 0 and p stays 0, which the rule counts as
+    converged after one iteration."""
+    pr = oracle.Problem(16, 16, 1, 1, alpha=10.0, inner=40)
+    st = oracle.dd_run(pr, np.full((16, 16), 0.3), 4, inner_tol=1e-6, record=True)
+    assert np.all(st.inner_counts == 1)
+    np.testing.assert_array_equal(st.u, np.full((16, 16), 0.3))
+
+
+def test_forced_counts_reproduce_fixed_and_adaptive_runs():
+    """Forcing every count to K gives the fixed-K run bit for bit; forcing the counts an
+    adaptive run recorded gives that run bit for bit."""
+    f, _ = synth.rof_image(40, 36, 5, 0.05, 4)
+    pr = oracle.Problem(40, 36, 3, 2, alpha=10.0, inner=30)
+    a = oracle.dd_run(pr, f, 5)
+    b = oracle.dd_run(pr, f, 5, counts=np.full((5, 6), 30))
+    assert np.array_equal(a.u, b.u) and np.array_equal(a.P1, b.P1) and np.array_equal(a.lamh, b.lamh)
+    c = oracle.dd_run(pr, f, 5, inner_tol=1e-3, record=True)
+    d = oracle.dd_run(pr, f, 5, counts=c.inner_counts, record=True)
+    assert np.array_equal(c.u, d.u) and np.array_equal(c.inner_counts, d.inner_counts)
+    assert c.inner_counts.min() < 30  # the rule did stop some solves early
