@@ -45,6 +45,48 @@ __device__ __forceinline__ void st_cluster_f64(uint32_t addr, double v) {
   asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
 }
 
+// Packed float32 pairs (sm_100+ `*.f32x2`): one instruction performs the operation on
+// two lanes, each rounded exactly as the scalar instruction, so packed and scalar code
+// give identical bits.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pk2(float lo, float hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float lo2(f32x2 v) {
+  float a, b;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+  return a;
+}
+__device__ __forceinline__ float hi2(f32x2 v) {
+  float a, b;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+  return b;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+// a * b + c, one rounding per lane (fmaf)
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
 template <bool RELEASE>
 __device__ __forceinline__ void cluster_arrive() {
   if (RELEASE)
@@ -1130,7 +1172,9 @@ struct PaLayout {
   static constexpr size_t BYTES = sizeof(float) * MB + 16;
 };
 
-template <int R, int TR, int CL, int FID, bool MASK>
+// PK: the inner loop works on packed pairs of rows (r, r + R/2) with `*.f32x2`
+// arithmetic (same bits as the scalar loop; the clamps stay scalar).
+template <int R, int TR, int CL, int FID, bool MASK, bool PK>
 __device__ __forceinline__ void fused_pa_body(const LocalArgs& A, const int first, const int stride) {
   using L = FullLayout<R, TR>;
   using P = PaLayout<R, TR>;
@@ -1291,52 +1335,155 @@ __device__ __forceinline__ void fused_pa_body(const LocalArgs& A, const int firs
     __syncthreads();  // staging consumed by every thread
     if (t + stride < T) prefetch(t + stride);
 
-    for (int k = 0; k < K; ++k) {
-      Coef c;
-      if (k < L::kMaxSmemCoef) {
-        const float4 ca = *reinterpret_cast<const float4*>(sCo + 8 * k);
-        const float4 cb = *reinterpret_cast<const float4*>(sCo + 8 * k + 4);
-        c = Coef{ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
-      } else {
-        c = A.coef[k];
-      }
-      if (need_qh && k > 0) wait_q();  // pbar1 halo of iteration k-1
+    if constexpr (PK) {
+      constexpr int H2 = R / 2;
+      static_assert(R % 2 == 0, "rows are paired");
+      f32x2 U[H2], P1v[H2], P2v[H2], H1v[H2], H2v[H2], Q1v[H2];
 #pragma unroll
-      for (int rr = 0; rr < R; ++rr) {
-        const int r = (rr + R - 1) % R;
-        const float below = r + 1 < R ? q1[r + 1] : sQ1[(ty + 1) * BW + j];
-        const float d = div_px(q1[r], below, sQ2r[r * L::QS], sQ2r[r * L::QS + 1]);
-        u[r] = u_update<FID>(u[r], d, sFr[r * BW], MASK && ((in_d >> r) & 1u), c);
-        sUr[r * L::US] = u[r];
-        if (rr == 0 && push_down) st_async_f32(remote_u, u[R - 1], remote_mbU);
+      for (int i = 0; i < H2; ++i) {
+        U[i] = pk2(u[i], u[i + H2]);
+        P1v[i] = pk2(p1[i], p1[i + H2]);
+        P2v[i] = pk2(p2[i], p2[i + H2]);
+        H1v[i] = pk2(h1[i], h1[i + H2]);
+        H2v[i] = pk2(h2[i], h2[i + H2]);
+        Q1v[i] = pk2(q1[i], q1[i + H2]);
       }
-      __syncthreads();
-      if (need_uh) wait_u();  // u halo of iteration k
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const float above = r > 0 ? u[r - 1] : sUr[-L::US];
-        p_update_lim(p1[r], q1[r], u[r] - above, h1[r], c, r == 0 ? lim_top : 1.f);
-        float q2;
-        p_update_lim(p2[r], q2, u[r] - sUr[r * L::US - 1], h2[r], c, lim_left);
-        sQ2r[r * L::QS] = q2;
-        if (r == 0) {
-          sQ1[ty * BW + j] = q1[0];
-          if (push_up) st_async_f32(remote_q1, q1[0], remote_mbQ);
+      for (int k = 0; k < K; ++k) {
+        Coef c;
+        if (k < L::kMaxSmemCoef) {
+          const float4 ca = *reinterpret_cast<const float4*>(sCo + 8 * k);
+          const float4 cb = *reinterpret_cast<const float4*>(sCo + 8 * k + 4);
+          c = Coef{ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+        } else {
+          c = A.coef[k];
         }
+        const f32x2 SIG = pk2(c.sig, c.sig), UA = pk2(c.ua, c.ua), UB = pk2(c.ub, c.ub);
+        const f32x2 PA = pk2(c.pa, c.pa), PC = pk2(c.pc, c.pc), PB = pk2(c.pb, c.pb), TH = pk2(c.th, c.th);
+        if (need_qh && k > 0) wait_q();  // pbar1 halo of iteration k-1
+        // u-step on row pairs; the pair holding the band's last row first
+#pragma unroll
+        for (int ii = 0; ii < H2; ++ii) {
+          const int i = (ii + H2 - 1) % H2;
+          const f32x2 below = i + 1 < H2 ? Q1v[i + 1] : pk2(hi2(Q1v[0]), sQ1[(ty + 1) * BW + j]);
+          const f32x2 left = pk2(sQ2r[i * L::QS], sQ2r[(i + H2) * L::QS]);
+          const f32x2 right = pk2(sQ2r[i * L::QS + 1], sQ2r[(i + H2) * L::QS + 1]);
+          const f32x2 d = sub2(add2(sub2(below, Q1v[i]), right), left);  // div_px
+          const f32x2 fg = pk2(sFr[i * BW], sFr[(i + H2) * BW]);
+          const f32x2 ub = fma2(SIG, d, U[i]);
+          f32x2 un;
+          if (FID == FID_L2) {
+            un = fma2(UB, fg, mul2(UA, ub));
+            if (MASK)
+              un = pk2(((in_d >> i) & 1u) ? lo2(ub) : lo2(un), ((in_d >> (i + H2)) & 1u) ? hi2(ub) : hi2(un));
+          } else {
+            un = pk2(prox_ubar<FID>(lo2(ub), lo2(fg), MASK && ((in_d >> i) & 1u), c),
+                     prox_ubar<FID>(hi2(ub), hi2(fg), MASK && ((in_d >> (i + H2)) & 1u), c));
+          }
+          U[i] = un;
+          sUr[i * L::US] = lo2(un);
+          sUr[(i + H2) * L::US] = hi2(un);
+          if (ii == 0 && push_down) st_async_f32(remote_u, hi2(un), remote_mbU);
+        }
+        __syncthreads();
+        if (need_uh) wait_u();  // u halo of iteration k
+        // p-step on row pairs; the pair holding the band's first row first
+#pragma unroll
+        for (int i = 0; i < H2; ++i) {
+          const f32x2 above = i > 0 ? U[i - 1] : pk2(sUr[-L::US], lo2(U[H2 - 1]));
+          const f32x2 leftu = pk2(sUr[i * L::US - 1], sUr[(i + H2) * L::US - 1]);
+          {
+            const f32x2 tt = fma2(PC, sub2(U[i], above), fma2(PA, P1v[i], mul2(PB, H1v[i])));  // p_target
+            const float l0 = i == 0 ? lim_top : 1.f;
+            const f32x2 pn = pk2(fminf(fmaxf(lo2(tt), -l0), l0), fminf(fmaxf(hi2(tt), -1.f), 1.f));
+            Q1v[i] = fma2(TH, sub2(pn, P1v[i]), pn);
+            P1v[i] = pn;
+          }
+          {
+            const f32x2 tt = fma2(PC, sub2(U[i], leftu), fma2(PA, P2v[i], mul2(PB, H2v[i])));
+            const f32x2 pn = pk2(fminf(fmaxf(lo2(tt), -lim_left), lim_left),
+                                 fminf(fmaxf(hi2(tt), -lim_left), lim_left));
+            const f32x2 q2 = fma2(TH, sub2(pn, P2v[i]), pn);
+            P2v[i] = pn;
+            sQ2r[i * L::QS] = lo2(q2);
+            sQ2r[(i + H2) * L::QS] = hi2(q2);
+          }
+          if (i == 0) {
+            const float q10 = lo2(Q1v[0]);
+            sQ1[ty * BW + j] = q10;
+            if (push_up) st_async_f32(remote_q1, q10, remote_mbQ);
+          }
+        }
+        if (last_row_here && s_bot) {
+          float qB;
+          p_update(pB, qB, -hi2(U[H2 - 1]), hB, c);
+          sQ1[TR * BW + j] = qB;
+        }
+        if (right_lane) {
+          const int lr = lr0 + j;
+          float pr = sPR[lr], qr;
+          p_update(pr, qr, -sU[(lr + 1) * L::US + 128], sHR[lr], c);
+          sPR[lr] = pr;
+          sQ2[lr * L::QS + 128] = qr;
+        }
+        __syncthreads();
       }
-      if (last_row_here && s_bot) {
-        float qB;
-        p_update(pB, qB, -u[R - 1], hB, c);
-        sQ1[TR * BW + j] = qB;
+#pragma unroll
+      for (int i = 0; i < H2; ++i) {
+        u[i] = lo2(U[i]);
+        u[i + H2] = hi2(U[i]);
+        p1[i] = lo2(P1v[i]);
+        p1[i + H2] = hi2(P1v[i]);
+        p2[i] = lo2(P2v[i]);
+        p2[i + H2] = hi2(P2v[i]);
       }
-      if (right_lane) {
-        const int lr = lr0 + j;
-        float pr = sPR[lr], qr;
-        p_update(pr, qr, -sU[(lr + 1) * L::US + 128], sHR[lr], c);
-        sPR[lr] = pr;
-        sQ2[lr * L::QS + 128] = qr;
+    } else {
+      for (int k = 0; k < K; ++k) {
+        Coef c;
+        if (k < L::kMaxSmemCoef) {
+          const float4 ca = *reinterpret_cast<const float4*>(sCo + 8 * k);
+          const float4 cb = *reinterpret_cast<const float4*>(sCo + 8 * k + 4);
+          c = Coef{ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+        } else {
+          c = A.coef[k];
+        }
+        if (need_qh && k > 0) wait_q();  // pbar1 halo of iteration k-1
+  #pragma unroll
+        for (int rr = 0; rr < R; ++rr) {
+          const int r = (rr + R - 1) % R;
+          const float below = r + 1 < R ? q1[r + 1] : sQ1[(ty + 1) * BW + j];
+          const float d = div_px(q1[r], below, sQ2r[r * L::QS], sQ2r[r * L::QS + 1]);
+          u[r] = u_update<FID>(u[r], d, sFr[r * BW], MASK && ((in_d >> r) & 1u), c);
+          sUr[r * L::US] = u[r];
+          if (rr == 0 && push_down) st_async_f32(remote_u, u[R - 1], remote_mbU);
+        }
+        __syncthreads();
+        if (need_uh) wait_u();  // u halo of iteration k
+  #pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const float above = r > 0 ? u[r - 1] : sUr[-L::US];
+          p_update_lim(p1[r], q1[r], u[r] - above, h1[r], c, r == 0 ? lim_top : 1.f);
+          float q2;
+          p_update_lim(p2[r], q2, u[r] - sUr[r * L::US - 1], h2[r], c, lim_left);
+          sQ2r[r * L::QS] = q2;
+          if (r == 0) {
+            sQ1[ty * BW + j] = q1[0];
+            if (push_up) st_async_f32(remote_q1, q1[0], remote_mbQ);
+          }
+        }
+        if (last_row_here && s_bot) {
+          float qB;
+          p_update(pB, qB, -u[R - 1], hB, c);
+          sQ1[TR * BW + j] = qB;
+        }
+        if (right_lane) {
+          const int lr = lr0 + j;
+          float pr = sPR[lr], qr;
+          p_update(pr, qr, -sU[(lr + 1) * L::US + 128], sHR[lr], c);
+          sPR[lr] = pr;
+          sQ2[lr * L::QS + 128] = qr;
+        }
+        __syncthreads();
       }
-      __syncthreads();
     }
     if (need_qh) wait_q();  // drain the last pbar1 halo (not read)
 
@@ -1369,9 +1516,9 @@ __device__ __forceinline__ void fused_pa_body(const LocalArgs& A, const int firs
   if (timed_out) atomicOr(A.err, 1);
 }
 
-template <int R, int TR, int CL, int MINB, int FID, bool MASK>
+template <int R, int TR, int CL, int MINB, int FID, bool MASK, bool PK>
 __global__ void __launch_bounds__(128 * TR, MINB) k_fused_pa(const LocalArgs A) {
-  fused_pa_body<R, TR, CL, FID, MASK>(A, blockIdx.y, gridDim.y);
+  fused_pa_body<R, TR, CL, FID, MASK, PK>(A, blockIdx.y, gridDim.y);
 }
 
 struct Config {
@@ -1388,7 +1535,7 @@ constexpr Config kConfigs[] = {
     {128, 8, 4, 4, "bw128_r8_tr4_cl4"},    // class 2, variant 1: 512 threads, 1 CTA/SM
     {128, 16, 2, 4, "bw128_r16_tr2_cl4"},  // class 2, variant 2: 256 threads, 16 rows/thread
 };
-constexpr int kNumVariants = 6;
+constexpr int kNumVariants = 10;
 
 template <int BW, int R, int TR, int CL, int FID, bool MASK, bool ADAPT>
 cudaError_t launch_one(const LocalArgs& a, cudaStream_t st) {
@@ -1505,19 +1652,19 @@ cudaError_t launch_async_batch(const BatchArgs& B, int total_tiles, cudaStream_t
 }
 
 // clusters of the persistent kernel resident at once, per device and instantiation
-template <int R, int TR, int CL, int MINB, int FID, bool MASK>
+template <int R, int TR, int CL, int MINB, int FID, bool MASK, bool PK>
 int& pa_clusters(int dev) {
   static int n[64] = {0};
   return n[dev & 63];
 }
 
-template <int R, int TR, int CL, int MINB, int FID, bool MASK>
+template <int R, int TR, int CL, int MINB, int FID, bool MASK, bool PK>
 cudaError_t launch_pa_one(const LocalArgs& a, cudaStream_t st) {
   using P = PaLayout<R, TR>;
   int dev = 0;
   cudaGetDevice(&dev);
   const int tiles = a.g.NR * a.g.NC;
-  int nc = pa_clusters<R, TR, CL, MINB, FID, MASK>(dev);
+  int nc = pa_clusters<R, TR, CL, MINB, FID, MASK, PK>(dev);
   if (nc <= 0 || nc > tiles) nc = tiles;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CL, nc, 1);
@@ -1531,24 +1678,24 @@ cudaError_t launch_pa_one(const LocalArgs& a, cudaStream_t st) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_fused_pa<R, TR, CL, MINB, FID, MASK>, a);
+  return cudaLaunchKernelEx(&cfg, k_fused_pa<R, TR, CL, MINB, FID, MASK, PK>, a);
 }
 
-template <int R, int TR, int CL, int MINB>
+template <int R, int TR, int CL, int MINB, bool PK>
 cudaError_t launch_pa(const LocalArgs& a, int fid, cudaStream_t st) {
   const bool m = a.mask != nullptr;
   switch (fid) {
-    case FID_L2: return m ? launch_pa_one<R, TR, CL, MINB, FID_L2, true>(a, st) : launch_pa_one<R, TR, CL, MINB, FID_L2, false>(a, st);
-    case FID_L1: return m ? launch_pa_one<R, TR, CL, MINB, FID_L1, true>(a, st) : launch_pa_one<R, TR, CL, MINB, FID_L1, false>(a, st);
-    default: return launch_pa_one<R, TR, CL, MINB, FID_SEG, false>(a, st);
+    case FID_L2: return m ? launch_pa_one<R, TR, CL, MINB, FID_L2, true, PK>(a, st) : launch_pa_one<R, TR, CL, MINB, FID_L2, false, PK>(a, st);
+    case FID_L1: return m ? launch_pa_one<R, TR, CL, MINB, FID_L1, true, PK>(a, st) : launch_pa_one<R, TR, CL, MINB, FID_L1, false, PK>(a, st);
+    default: return launch_pa_one<R, TR, CL, MINB, FID_SEG, false, PK>(a, st);
   }
 }
 
 // shared-memory opt-in, and how many clusters fit at once (0 disables persistence)
-template <int R, int TR, int CL, int MINB, int FID, bool MASK>
+template <int R, int TR, int CL, int MINB, int FID, bool MASK, bool PK>
 cudaError_t prepare_pa_one() {
   using P = PaLayout<R, TR>;
-  auto kern = k_fused_pa<R, TR, CL, MINB, FID, MASK>;
+  auto kern = k_fused_pa<R, TR, CL, MINB, FID, MASK, PK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::BYTES);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -1569,18 +1716,18 @@ cudaError_t prepare_pa_one() {
   }
   int dev = 0;
   cudaGetDevice(&dev);
-  pa_clusters<R, TR, CL, MINB, FID, MASK>(dev) = n;
+  pa_clusters<R, TR, CL, MINB, FID, MASK, PK>(dev) = n;
   return cudaSuccess;
 }
 
-template <int R, int TR, int CL, int MINB>
+template <int R, int TR, int CL, int MINB, bool PK>
 cudaError_t prepare_pa() {
   cudaError_t e;
-  if ((e = prepare_pa_one<R, TR, CL, MINB, FID_L2, false>()) != cudaSuccess) return e;
-  if ((e = prepare_pa_one<R, TR, CL, MINB, FID_L2, true>()) != cudaSuccess) return e;
-  if ((e = prepare_pa_one<R, TR, CL, MINB, FID_L1, false>()) != cudaSuccess) return e;
-  if ((e = prepare_pa_one<R, TR, CL, MINB, FID_L1, true>()) != cudaSuccess) return e;
-  return prepare_pa_one<R, TR, CL, MINB, FID_SEG, false>();
+  if ((e = prepare_pa_one<R, TR, CL, MINB, FID_L2, false, PK>()) != cudaSuccess) return e;
+  if ((e = prepare_pa_one<R, TR, CL, MINB, FID_L2, true, PK>()) != cudaSuccess) return e;
+  if ((e = prepare_pa_one<R, TR, CL, MINB, FID_L1, false, PK>()) != cudaSuccess) return e;
+  if ((e = prepare_pa_one<R, TR, CL, MINB, FID_L1, true, PK>()) != cudaSuccess) return e;
+  return prepare_pa_one<R, TR, CL, MINB, FID_SEG, false, PK>();
 }
 
 template <int R, int TR, int CL, int MINB, int FID, bool MASK>
@@ -1697,8 +1844,12 @@ cudaError_t fused_prepare() {
   if ((e = prepare_full<8, 4, 4, 1>()) != cudaSuccess) return e;
   if ((e = prepare_async<8, 2, 8, 2>()) != cudaSuccess) return e;
   if ((e = prepare_async<8, 4, 4, 1>()) != cudaSuccess) return e;
-  if ((e = prepare_pa<8, 2, 8, 2>()) != cudaSuccess) return e;
-  if ((e = prepare_pa<8, 4, 4, 1>()) != cudaSuccess) return e;
+  if ((e = prepare_pa<8, 2, 8, 2, true>()) != cudaSuccess) return e;
+  if ((e = prepare_pa<8, 2, 8, 2, false>()) != cudaSuccess) return e;
+  if ((e = prepare_pa<8, 4, 4, 1, false>()) != cudaSuccess) return e;
+  if ((e = prepare_pa<4, 4, 8, 2, true>()) != cudaSuccess) return e;
+  if ((e = prepare_pa<16, 1, 8, 2, true>()) != cudaSuccess) return e;
+  if ((e = prepare_pa<8, 2, 8, 3, true>()) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_fused_async_batch<8, 2, 8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)AsyncLayout<8, 2>::BYTES)) != cudaSuccess)
     return e;
@@ -1717,12 +1868,16 @@ cudaError_t launch_fused_local(const LocalArgs& a, int fid, int variant, cudaStr
   if (a.inner_tol2 > 0.0) variant = 0;  // adaptive stopping: the cluster-barrier kernel only
   if (a.inner_tol2 <= 0.0 && a.g.H == 128 * a.g.NR && a.g.W == 128 * a.g.NC) {  // every tile exactly 128 x 128
     switch (variant) {
-      case 0: return launch_pa<8, 2, 8, 2>(a, fid, st);     // persistent, async halos, prefetch: 256 threads
-      case 1: return launch_async<8, 2, 8, 2>(a, fid, st);  // async halos, one subdomain per cluster
-      case 2: return launch_full<8, 4, 4, 1>(a, fid, st);   // cluster barrier per half-step: 512 threads
-      case 3: return launch_wr<2, 8, 8, 2>(a, fid, st);     // warp rows, per-warp mbarriers
-      case 4: return launch_pa<8, 4, 4, 1>(a, fid, st);     // persistent, async halos, prefetch: 512 threads
-      case 5: return launch_async<8, 4, 4, 1>(a, fid, st);  // async halos: 512 threads
+      case 0: return launch_pa<8, 2, 8, 2, true>(a, fid, st);   // persistent, async halos, prefetch, packed pairs
+      case 1: return launch_async<8, 2, 8, 2>(a, fid, st);      // async halos, one subdomain per cluster
+      case 2: return launch_full<8, 4, 4, 1>(a, fid, st);       // cluster barrier per half-step: 512 threads
+      case 3: return launch_wr<2, 8, 8, 2>(a, fid, st);         // warp rows, per-warp mbarriers
+      case 4: return launch_pa<8, 4, 4, 1, false>(a, fid, st);  // persistent, async halos, prefetch: 512 threads
+      case 5: return launch_async<8, 4, 4, 1>(a, fid, st);      // async halos: 512 threads
+      case 6: return launch_pa<8, 2, 8, 2, false>(a, fid, st);  // variant 0 with scalar arithmetic
+      case 7: return launch_pa<4, 4, 8, 2, true>(a, fid, st);   // packed, 4 rows per thread: 512 threads, 2 CTAs/SM
+      case 8: return launch_pa<16, 1, 8, 2, true>(a, fid, st);  // packed, 16 rows per thread: 128 threads
+      case 9: return launch_pa<8, 2, 8, 3, true>(a, fid, st);   // variant 0 at 3 CTAs per SM (85 registers)
       default: return cudaErrorInvalidValue;
     }
   }

@@ -34,8 +34,16 @@ __device__ __forceinline__ float div_px(float top, float bot, float left, float 
 // fg is f (L2, L1) or g = (f - c1)^2 - (f - c2)^2 (SEG); in_d marks the inpainting
 // domain D, where the L2/L1 fidelity vanishes and the prox is the identity.
 template <int FID>
+__device__ __forceinline__ float prox_ubar(float ubar, float fg, bool in_d, const Coef& c);
+
+template <int FID>
 __device__ __forceinline__ float u_update(float u, float d, float fg, bool in_d, const Coef& c) {
-  const float ubar = fmaf(c.sig, d, u);
+  return prox_ubar<FID>(fmaf(c.sig, d, u), fg, in_d, c);
+}
+
+// prox_{sigma_k alpha F} at ubar = u + sigma_k div pbar
+template <int FID>
+__device__ __forceinline__ float prox_ubar(float ubar, float fg, bool in_d, const Coef& c) {
   if (FID == FID_SEG) {
     const float x = fmaf(-c.s, fg, ubar);
     return fminf(fmaxf(x, 0.0f), 1.0f);
