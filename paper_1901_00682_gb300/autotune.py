@@ -113,3 +113,40 @@ def tune(f, problem, tol=1e-4, j_ref=None, tiles=(64, 128), inners=(5, 10, 20), 
         trials.append(Trial(tile, inner, variant, ms if reached else math.inf, st.outer_done, st.rel_err, reached))
     best = pick_best(trials)
     return TuneResult(best, trials, j_ref, tol)
+
+
+def time_variants(f, problem, sub_rows, sub_cols, variants, inner=10, outer=100, warmup=8, stream=None):
+    """Average device time of one outer iteration (CUDA-graph replay, CUDA events on
+    the solver's stream) for each hardware mapping; f is a device tensor."""
+    import torch
+    H, W = f.shape
+    out = {}
+    for v in variants:
+        p = L.make_params(H, W, sub_rows, sub_cols, inner_iters=inner, variant=v, **problem)
+        s = L.Solver(p, stream)
+        st = torch.cuda.current_stream() if stream is None else stream
+        s.load(f)
+        s.iterate(warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        s.iterate(outer)
+        e1.record(st)
+        e1.synchronize()
+        out[v] = e0.elapsed_time(e1) / outer
+        s.close()
+    return out
+
+
+if __name__ == "__main__":
+    # Times the fused hardware mappings on the 4096^2 ROF workload (32 x 32 subdomains
+    # of 128^2, alpha 8, K = 10): python -m paper_1901_00682_gb300.autotune [v,v,...]
+    import sys
+
+    import torch
+
+    import synth
+    vs = [int(x) for x in sys.argv[1].split(",")] if len(sys.argv) > 1 else list(range(10))
+    img, _ = synth.rof_image(4096, 4096, 400, 0.1, 0)
+    ms = time_variants(torch.from_numpy(img).cuda(), dict(fidelity="l2", alpha=8.0), 32, 32, vs)
+    for v, t in ms.items():
+        print(f"variant {v}: {t:.4f} ms per outer iteration ({4096 * 4096 * 10 / t / 1e3:.0f} Mpixel*iter/s)")
