@@ -172,11 +172,6 @@ def cpu_baseline(f, outer=2):
                       f"FP64, OpenMP over subdomains, {dt:.1f} s"}
 
 
-# Algorithmic HBM bytes per pixel and inner iteration of the reverse pass: the tape
-# recomputation (u-step 24 B, p-step 38 B) and the two reverse kernels (62 B, 54 B).
-ADJ_BYTES_PER_PX_INNER = 24 + 38 + 62 + 54
-
-
 def measure_adjoint(dev):
     """Forward and backward time of the unrolled solver on the differentiation workload:
     8 ROF images 1024 x 1024 (sigma 0.08, alpha 10), 8 x 8 subdomains, 100 outer x 10
@@ -215,8 +210,9 @@ def measure_adjoint(dev):
                         "checkpoint every 10, loss 1/2||u_K - g||^2, dL/df and dL/dalpha",
             "ms_forward": ms_f, "ms_backward": ms_b, "backward_over_forward": ms_b / ms_f,
             "backward_Mpixel_iter_per_s": px_it / (ms_b * 1e-3) / 1e6,
-            "backward_effective_hbm_gbs": px_it * ADJ_BYTES_PER_PX_INNER / (ms_b * 1e-3) / 1e9,
-            "algorithmic_bytes_per_pixel_inner": ADJ_BYTES_PER_PX_INNER,
+            "backward_work": "per outer iteration: the segment's forward recomputation (fused path) and one "
+                             "tile-fused kernel that recomputes the K inner iterations with the tape in L2 and "
+                             "runs their K reverse iterations",
             "timing": "host wall clock with device synchronisation, best of 2 after one warm-up"}
 
 

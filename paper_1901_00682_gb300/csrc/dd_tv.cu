@@ -39,6 +39,9 @@ struct AdjointWork {
   float *AP = nullptr, *AQ = nullptr, *APh = nullptr;  // n1 + n2 each
   float *AL = nullptr, *APp = nullptr;                 // nh + nv, 2 (nh + nv)
   int4 *rowtab = nullptr, *coltab = nullptr;           // H, W: tile index, first, end
+  bool fused = false;   // the tile-fused reverse kernel applies
+  float* tapeF = nullptr;  // its tape
+  int nal = 0;          // alpha partial-sum slots
   // one graph per segment (recompute + reverse of its outer iterations), valid for
   // the (N, m, mask) they were captured with
   std::vector<cudaGraphExec_t> graphs;
@@ -460,7 +463,7 @@ void adj_free(AdjointWork* w) {
   if (!w) return;
   adj_drop_graphs(w);
   void* bufs[] = {w->ck, w->seg, w->ubar, w->M, w->Ph, w->Pb, w->Au, w->Ad, w->Af, w->Aal, w->AP, w->AQ, w->APh,
-                  w->AL, w->APp, w->rowtab, w->coltab};
+                  w->AL, w->APp, w->rowtab, w->coltab, w->tapeF};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete w;
@@ -475,32 +478,47 @@ int adj_reserve(dd_tv* h, int nck, int m) {
     h->adj = w;
     const size_t K = (size_t)h->p.inner_iters, nP = h->n1 + h->n2, ne = h->nh + h->nv;
     w->slot = h->npx + nP + 5 * ne;
+    const size_t tape_f = adj_fused_tape_floats(h->g, h->p.inner_iters);
+    // the fused reverse kernel keeps a per-CTA tape; beyond 4 GiB use the per-step path
+    w->fused = tape_f > 0 && tape_f * sizeof(float) <= (4ull << 30);
+    w->nal = std::max(adj_alpha_slots(h->g), adj_alpha_slots_fused(h->g));
+    if (w->fused) CK(adj_fused_prepare());
     int rc;
-    if ((rc = dalloc(h, &w->ubar, K * h->npx)) || (rc = dalloc(h, &w->M, K * nP)) ||
-        (rc = dalloc(h, &w->Au, h->npx)) || (rc = dalloc(h, &w->Ad, h->npx)) || (rc = dalloc(h, &w->Af, h->npx)) ||
-        (rc = dalloc(h, &w->Aal, (size_t)adj_alpha_slots(h->g))) || (rc = dalloc(h, &w->rowtab, h->g.H)) ||
-        (rc = dalloc(h, &w->coltab, h->g.W)) || (rc = dalloc(h, &w->AP, nP)) || (rc = dalloc(h, &w->AQ, nP)) ||
+    if ((rc = dalloc(h, &w->Au, h->npx)) || (rc = dalloc(h, &w->Ad, h->npx)) || (rc = dalloc(h, &w->Af, h->npx)) ||
+        (rc = dalloc(h, &w->Aal, (size_t)w->nal)) || (rc = dalloc(h, &w->AP, nP)) || (rc = dalloc(h, &w->AQ, nP)) ||
         (rc = dalloc(h, &w->APh, nP)) || (rc = dalloc(h, &w->AL, ne)) || (rc = dalloc(h, &w->APp, 2 * ne))) {
       adj_free(w);
       h->adj = nullptr;
       return rc;
     }
-    if (!h->Ph1 && ((rc = dalloc(h, &w->Ph, nP)) || (rc = dalloc(h, &w->Pb, nP)))) {
-      adj_free(w);
-      h->adj = nullptr;
-      return rc;
+    if (w->fused) {
+      if ((rc = dalloc(h, &w->tapeF, tape_f))) {
+        adj_free(w);
+        h->adj = nullptr;
+        return rc;
+      }
+    } else {
+      // per-step reverse: the tape in global memory, the plain path's phat / pbar, and
+      // the tile tables of the per-pixel kernels
+      if ((rc = dalloc(h, &w->ubar, K * h->npx)) || (rc = dalloc(h, &w->M, K * nP)) ||
+          (rc = dalloc(h, &w->rowtab, h->g.H)) || (rc = dalloc(h, &w->coltab, h->g.W)) ||
+          (!h->Ph1 && ((rc = dalloc(h, &w->Ph, nP)) || (rc = dalloc(h, &w->Pb, nP))))) {
+        adj_free(w);
+        h->adj = nullptr;
+        return rc;
+      }
+      // inactive dofs are never written by the tape: their pass bits stay 0
+      CK(cudaMemsetAsync(w->M, 0, K * nP, h->stream));
+      std::vector<int4> rt(h->g.H), ct(h->g.W);
+      for (int a = 0; a < h->g.NR; ++a)
+        for (int i = part_start(a, h->g.H, h->g.NR); i < part_start(a + 1, h->g.H, h->g.NR); ++i)
+          rt[i] = make_int4(a, part_start(a, h->g.H, h->g.NR), part_start(a + 1, h->g.H, h->g.NR), 0);
+      for (int b = 0; b < h->g.NC; ++b)
+        for (int j = part_start(b, h->g.W, h->g.NC); j < part_start(b + 1, h->g.W, h->g.NC); ++j)
+          ct[j] = make_int4(b, part_start(b, h->g.W, h->g.NC), part_start(b + 1, h->g.W, h->g.NC), 0);
+      CK(cudaMemcpy(w->rowtab, rt.data(), rt.size() * sizeof(int4), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(w->coltab, ct.data(), ct.size() * sizeof(int4), cudaMemcpyHostToDevice));
     }
-    // inactive dofs are never written by the tape: their pass bits stay 0
-    CK(cudaMemsetAsync(w->M, 0, K * nP, h->stream));
-    std::vector<int4> rt(h->g.H), ct(h->g.W);
-    for (int a = 0; a < h->g.NR; ++a)
-      for (int i = part_start(a, h->g.H, h->g.NR); i < part_start(a + 1, h->g.H, h->g.NR); ++i)
-        rt[i] = make_int4(a, part_start(a, h->g.H, h->g.NR), part_start(a + 1, h->g.H, h->g.NR), 0);
-    for (int b = 0; b < h->g.NC; ++b)
-      for (int j = part_start(b, h->g.W, h->g.NC); j < part_start(b + 1, h->g.W, h->g.NC); ++j)
-        ct[j] = make_int4(b, part_start(b, h->g.W, h->g.NC), part_start(b + 1, h->g.W, h->g.NC), 0);
-    CK(cudaMemcpy(w->rowtab, rt.data(), rt.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(w->coltab, ct.data(), ct.size() * sizeof(int4), cudaMemcpyHostToDevice));
   }
   AdjointWork* w = h->adj;
   if (nck > w->cap_ck || m > w->cap_seg) adj_drop_graphs(w);  // they hold the slot addresses
@@ -585,17 +603,27 @@ AdjArgs adj_args(dd_tv* h) {
   r.APp = Strips{w->APp, w->APp + h->nh, w->APp + 2 * h->nh, w->APp + 2 * h->nh + h->nv};
   r.rowtab = w->rowtab;
   r.coltab = w->coltab;
+  r.tape = w->tapeF;
   return r;
 }
 
-// Recomputes outer iteration n from the state in the handle's buffers (h->n = n) with
-// the plain path's kernels, recording the tape of its local solves.
-int tape_outer(dd_tv* h) {
+// Recomputes outer iteration n from the state in the handle's buffers (h->n = n) and
+// runs the reverse of its local solves: in one tile-fused kernel (tape in shared
+// memory) when the tile shape and K allow, else with the plain path's kernels
+// recording the tape in global memory followed by the global-memory reverse kernels.
+int reverse_outer(dd_tv* h, const AdjArgs& r);
+
+int tape_outer(dd_tv* h, const AdjArgs& r) {
   AdjointWork* w = h->adj;
   const cudaStream_t st = h->stream;
   const int par = h->n & 1;
   CK(launch_interface(h->g, (float)h->p.sigma, h->strips[par], h->strips[1 - par], h->lamh, h->lamv, st));
   LocalArgs a = local_args(h, 1 - par);
+  if (w->fused) {
+    CK(launch_adj_fused(a, r, h->fid, st));
+    CK(launch_adj_interface(r, (float)h->p.sigma, (float)h->p.tau, st));
+    return DD_TV_OK;
+  }
   const size_t nP = h->n1 + h->n2;
   float* Ph1 = h->Ph1 ? h->Ph1 : w->Ph;
   float* Ph2 = h->Ph1 ? h->Ph2 : w->Ph + h->n1;
@@ -607,10 +635,10 @@ int tape_outer(dd_tv* h) {
     CK(launch_ustep_tape(a, w->rowtab, w->coltab, Pb1, Pb2, h->coef + k, h->fid, w->ubar + (size_t)k * h->npx, st));
     CK(launch_pstep_tape(a, w->rowtab, w->coltab, Ph1, Ph2, Pb1, Pb2, h->coef + k, Mk, Mk + h->n1, st));
   }
-  return DD_TV_OK;
+  return reverse_outer(h, r);
 }
 
-// Reverse of outer iteration n (after tape_outer).
+// Reverse of outer iteration n from the tape in global memory (after tape_outer).
 int reverse_outer(dd_tv* h, const AdjArgs& r) {
   AdjointWork* w = h->adj;
   const cudaStream_t st = h->stream;
@@ -639,8 +667,7 @@ int adj_segment(dd_tv* h, const AdjArgs& r, int c) {
   }
   for (int n = e0 - 1; n >= s0; --n) {
     if ((rc = state_restore(h, w->seg + (size_t)(n - s0) * w->slot, n))) return rc;
-    if ((rc = tape_outer(h))) return rc;
-    if ((rc = reverse_outer(h, r))) return rc;
+    if ((rc = tape_outer(h, r))) return rc;
   }
   return DD_TV_OK;
 }
@@ -1019,7 +1046,7 @@ int dd_tv_adjoint_backward(dd_tv* h, const float* grad_u_dev, float* grad_f_dev,
   const cudaStream_t st = h->stream;
   const size_t nP = h->n1 + h->n2, ne = h->nh + h->nv;
   CK(cudaMemcpyAsync(w->Au, grad_u_dev, h->npx * sizeof(float), cudaMemcpyDeviceToDevice, st));
-  const int nal = adj_alpha_slots(h->g);
+  const int nal = w->nal;
   CK(cudaMemsetAsync(w->Af, 0, h->npx * sizeof(float), st));
   CK(cudaMemsetAsync(w->Aal, 0, nal * sizeof(double), st));
   CK(cudaMemsetAsync(w->AP, 0, nP * sizeof(float), st));

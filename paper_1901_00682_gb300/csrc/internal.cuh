@@ -84,6 +84,7 @@ struct AdjArgs {
   float *APh1, *APh2;      // phat
   float *ALh, *ALv;        // lambda
   Strips APp;              // interface values of p~^{n-1}
+  float* tape;             // tile-fused reverse kernel: adj_fused_tape_floats(g, K) floats
 };
 
 // ---- kernels_interface.cu
@@ -155,6 +156,19 @@ cudaError_t launch_sum_f64(const double* x, long long n, double* partials, unsig
 int sum_f64_partials_count();
 // number of float64 partial sums the reverse u-kernel keeps for an image grid
 int adj_alpha_slots(const Grid& g);
+
+// ---- kernels_adjoint_fused.cu
+// Reverse of one outer iteration's local solves, tape in shared memory: a = the local
+// solve's arguments (state after the multiplier update), z = the adjoint fields (Au,
+// AP1/AP2 in: adjoints of u^{n+1}, p~^{n+1}; out: of u^n and of p~^n through the local
+// solve; APh1/APh2 out on the subdomain sides; Af +=; Aal += per (tile, CTA) slot).
+cudaError_t launch_adj_fused(const LocalArgs& a, const AdjArgs& z, int fidelity, cudaStream_t st);
+// floats of the fused reverse kernel's tape (0 if the tile shape is not supported)
+size_t adj_fused_tape_floats(const Grid& g, int K);
+// shared-memory opt-in of the fused reverse kernels (outside any stream capture)
+cudaError_t adj_fused_prepare();
+// alpha partial-sum slots the fused reverse kernel uses
+int adj_alpha_slots_fused(const Grid& g);
 
 // ---- kernels_misc.cu
 // u0 = f (0 on D) for L2/L1, 1/2 for SEG

@@ -38,11 +38,11 @@ def _extra(fid):
     return dict(c1=0.2, c2=0.8) if fid == "seg" else {}
 
 
-def _gpu(f, g, mask, NR, NC, N, fid, every=5, path="fused", alpha=None):
+def _gpu(f, g, mask, NR, NC, N, fid, every=5, path="fused", alpha=None, K=10):
     from paper_1901_00682_gb300 import _lib as L
     H, W = f.shape
     a = ALPHA[fid] if alpha is None else alpha
-    p = L.make_params(H, W, NR, NC, fidelity=fid, alpha=a, path=path, **_extra(fid))
+    p = L.make_params(H, W, NR, NC, fidelity=fid, alpha=a, path=path, inner_iters=K, **_extra(fid))
     fd = torch.from_numpy(f).cuda()
     md = None if mask is None else torch.from_numpy(mask).cuda()
     with L.Solver(p) as s:
@@ -55,12 +55,12 @@ def _gpu(f, g, mask, NR, NC, N, fid, every=5, path="fused", alpha=None):
         return u.cpu().numpy().astype(np.float64), gf.cpu().numpy().astype(np.float64), ga
 
 
-def _ref(f, g, mask, NR, NC, N, fid, alpha=None):
+def _ref(f, g, mask, NR, NC, N, fid, alpha=None, K=10):
     a = ALPHA[fid] if alpha is None else alpha
     ft = torch.tensor(f.astype(np.float64), requires_grad=True)
     at = torch.tensor(a, dtype=torch.float64, requires_grad=True)
     mt = None if mask is None else torch.tensor(mask == 1)
-    u = UT.unrolled(ft, at, NR, NC, N, fidelity=fid, mask=mt, **_extra(fid))
+    u = UT.unrolled(ft, at, NR, NC, N, fidelity=fid, mask=mt, K=K, **_extra(fid))
     (0.5 * ((u - torch.tensor(g.astype(np.float64))) ** 2).sum()).backward()
     return u.detach().numpy(), ft.grad.numpy(), at.grad.item()
 
@@ -69,20 +69,27 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-@pytest.mark.parametrize("fid,mask_prob,shape,tiles,alpha", [
-    ("l2", 0.0, (48, 40), (3, 2), None),
-    ("l2", 0.0, (50, 37), (3, 2), None),      # ragged tiles
-    ("l2", 0.2, (48, 40), (3, 2), None),      # inpainting domain
+@pytest.mark.parametrize("fid,mask_prob,shape,tiles,alpha,K,path", [
+    ("l2", 0.0, (48, 40), (3, 2), None, 10, "fused"),
+    ("l2", 0.0, (50, 37), (3, 2), None, 10, "fused"),      # ragged tiles
+    ("l2", 0.2, (48, 40), (3, 2), None, 10, "fused"),      # inpainting domain
     # segmentation with alpha 20 saturates every pixel at 0 or 1 within a few outer
     # iterations (zero derivative); alpha 1 keeps about 12% of the pixels inside (0, 1)
-    ("seg", 0.0, (48, 40), (2, 2), 1.0),
+    ("seg", 0.0, (48, 40), (2, 2), 1.0, 10, "fused"),
+    ("l2", 0.0, (100, 90), (2, 2), None, 6, "fused"),      # 50 x 45 tiles: the 64-column mapping
+    ("l2", 0.0, (256, 256), (2, 2), None, 4, "fused"),     # 128 x 128 tiles: clusters of 8 CTAs
+    ("l2", 0.0, (128, 128), (2, 2), None, 16, "fused"),
+    # 80 x 150 tiles are wider than the tile-fused reverse kernel: the tape is recorded
+    # in global memory by the plain path's kernels and reversed by the per-step kernels
+    ("l2", 0.0, (160, 150), (2, 1), None, 6, "plain"),
+    ("l2", 0.2, (160, 150), (2, 1), None, 6, "plain"),
 ])
-def test_adjoint_matches_fp64_autograd(cuda_lib, fid, mask_prob, shape, tiles, alpha):
+def test_adjoint_matches_fp64_autograd(cuda_lib, fid, mask_prob, shape, tiles, alpha, K, path):
     H, W = shape
     f, g, mask = _case(H, W, fid, mask_prob, seed=0 if fid == "seg" else 3)
-    N = 12
-    u, gf, ga = _gpu(f, g, mask, *tiles, N, fid, alpha=alpha)
-    ur, gfr, gar = _ref(f, g, mask, *tiles, N, fid, alpha=alpha)
+    N = 12 if H * W < 10000 else 4
+    u, gf, ga = _gpu(f, g, mask, *tiles, N, fid, alpha=alpha, K=K, path=path)
+    ur, gfr, gar = _ref(f, g, mask, *tiles, N, fid, alpha=alpha, K=K)
     assert np.abs(u - ur).max() <= 5e-4
     assert gar != 0.0 and np.abs(gfr).max() > 0.0
     rf, ra = _rel(gf, gfr), abs(ga - gar) / abs(gar)
