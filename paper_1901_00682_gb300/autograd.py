@@ -119,3 +119,36 @@ class _UnrolledFn(torch.autograd.Function):
             t = t.sum() if len(ctx.alpha_shape) == 0 or ctx.alpha_shape.numel() == 1 else t
             g_alpha = t.reshape(ctx.alpha_shape).to(dtype=ctx.alpha_dtype, device=gu.device)
         return (gf if ctx.needs_input_grad[0] else None), g_alpha, None, None
+
+
+if __name__ == "__main__":
+    # Forward + backward of the unrolled solver on synthetic ROF images (the
+    # differentiation workload's recipe) and their wall times:
+    #   python -m paper_1901_00682_gb300.autograd [images] [side] [outer] [checkpoint_every]
+    import sys
+    import time
+
+    import numpy as np
+
+    import synth
+    args = [int(x) for x in sys.argv[1:]]
+    B, S, N, M = (args + [8, 1024, 100, 10][len(args):])[:4]
+    pairs = [synth.rof_image(S, S, max(4, 400 * S * S // (4096 * 4096)), 0.08, 500 + b) for b in range(B)]
+    f = torch.from_numpy(np.stack([p[0] for p in pairs])).cuda().requires_grad_(True)
+    g = torch.from_numpy(np.stack([p[1] for p in pairs])).cuda()
+    alpha = torch.tensor(10.0, dtype=torch.float64, device="cuda", requires_grad=True)
+    mod = UnrolledDDTV(S, S, S // 128, S // 128, N, checkpoint_every=M)
+    for rep in range(2):
+        f.grad = None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        u = mod(f, alpha)
+        loss = 0.5 * ((u - g) ** 2).sum()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        loss.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+    print(f"{B} x {S}^2, {N} outer: forward {1e3 * (t1 - t0):.2f} ms, backward {1e3 * (t2 - t1):.2f} ms, "
+          f"loss {loss.item():.6e}, dL/dalpha {alpha.grad.item():.6e}")
+    mod.close()

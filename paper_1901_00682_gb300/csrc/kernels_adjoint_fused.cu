@@ -349,7 +349,13 @@ __global__ void __launch_bounds__(BW* TR, MINB) k_adj_fused(const LocalArgs A, c
     const float opq = 1.0f + c.th;
     const uint32_t bits = tapeM[(size_t)k * NT + tid];
     const float* tU = tapeU + (size_t)k * R * NT;
+    float ubk[R];  // this iteration's tape, loaded before the barrier wait hides its latency
+#pragma unroll
+    for (int r = 0; r < R; ++r) ubk[r] = tU[r * NT + tid];
     const bool first = k == K - 1, last = k == 0;
+    // the next (earlier) iteration's pass bits and theta, for the a_t it will read
+    const uint32_t bn = k > 0 ? tapeM[(size_t)(k - 1) * NT + tid] : 0u;
+    const float opn = k > 0 ? 1.0f + A.coef[k - 1].th : 0.0f;
     float Ad[R];
     // reverse u-step: Au' = Au - div(pc a_t); the band's last row first (row below)
     auto ru_px = [&](int r) {
@@ -365,8 +371,7 @@ __global__ void __launch_bounds__(BW* TR, MINB) k_adj_fused(const LocalArgs A, c
       const float dv = div_px(c.pc * at_top, c.pc * at_bot, c.pc * at_left, c.pc * at_right);
       const float aun = Au[r] - dv;
       float dub, df, dal;
-      prox_partials_fg<FID>(tU[r * NT + tid], sF[lr * BW + j], MASK && ((in_d >> r) & 1u), A.c1, A.c2, c, dub,
-                            df, dal);
+      prox_partials_fg<FID>(ubk[r], sF[lr * BW + j], MASK && ((in_d >> r) & 1u), A.c1, A.c2, c, dub, df, dal);
       const float aub = dub * aun;
       Au[r] = aub;
       Ad[r] = c.sig * aub;
@@ -393,21 +398,25 @@ __global__ void __launch_bounds__(BW* TR, MINB) k_adj_fused(const LocalArgs A, c
       const float ad_left = sU[lr * L::US + j];      // 0 left of the tile's first column
       adj_dof_reg(AP1[r], AQ1[r], AH1[r], (bits >> r) & 1u, ad_above - Ad[r], c, opq, first, last);
       adj_dof_reg(AP2[r], AQ2[r], AH2[r], (bits >> (8 + r)) & 1u, ad_left - Ad[r], c, opq, first, last);
-      if (r == rb && s_bot) adj_dof_reg(APB, AQB, AHB, (bits >> 16) & 1u, Ad[r], c, opq, first, last);
+      // a_t of the p2 dof for iteration k-1 (the left neighbour has read iteration k's)
+      if (k > 0 && col_ok) sQ2[lr * L::QS + j] = ((bn >> (8 + r)) & 1u) ? AP2[r] + opn * AQ2[r] : 0.0f;
+      if (r == rb && s_bot) {
+        adj_dof_reg(APB, AQB, AHB, (bits >> 16) & 1u, Ad[r], c, opq, first, last);
+        if (k > 0) atB = ((bn >> 16) & 1u) ? APB + opn * AQB : 0.0f;
+      }
       if (right_thr) {
         float ap = sPR[lr], aq = sHR[lr], ah = sXR[lr];
         adj_dof_reg(ap, aq, ah, (bits >> (17 + r)) & 1u, Ad[r], c, opq, first, last);
         sPR[lr] = ap;
         sHR[lr] = aq;
         sXR[lr] = ah;
+        if (k > 0) sQ2[lr * L::QS + mc] = ((bn >> (17 + r)) & 1u) ? ap + opn * aq : 0.0f;
       }
     };
     if (CL > 1) cl_wait();
     rp_px(0);
     if (k > 0) {  // row 0's a_t for iteration k-1 feeds the thread row / CTA above
-      const Coef cn = A.coef[k - 1];
-      const uint32_t bn = tapeM[(size_t)(k - 1) * NT + tid];
-      const float at10 = (bn & 1u) ? AP1[0] + (1.0f + cn.th) * AQ1[0] : 0.0f;
+      const float at10 = (bn & 1u) ? AP1[0] + opn * AQ1[0] : 0.0f;
       sQ1[ty * BW + j] = at10;
       if (push_up) st_remote(remote_q1h, at10);
     }
@@ -416,21 +425,7 @@ __global__ void __launch_bounds__(BW* TR, MINB) k_adj_fused(const LocalArgs A, c
     }
 #pragma unroll
     for (int r = 1; r < R; ++r) rp_px(r);
-    __syncthreads();  // every thread has read the Ad of its neighbours
-    if (k > 0) {
-      // a_t of the p2 dofs (and the right side, the bottom side) for iteration k-1
-      const Coef cn = A.coef[k - 1];
-      const float opn = 1.0f + cn.th;
-      const uint32_t bn = tapeM[(size_t)(k - 1) * NT + tid];
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int lr = lr0 + r;
-        if (col_ok) sQ2[lr * L::QS + j] = ((bn >> (8 + r)) & 1u) ? AP2[r] + opn * AQ2[r] : 0.0f;
-        if (right_thr) sQ2[lr * L::QS + mc] = ((bn >> (17 + r)) & 1u) ? sPR[lr] + opn * sHR[lr] : 0.0f;
-      }
-      if (rb >= 0 && rb < R) atB = (s_bot && ((bn >> 16) & 1u)) ? APB + opn * AQB : 0.0f;
-      __syncthreads();
-    }
+    __syncthreads();  // every thread has read the Ad of its neighbours and published its a_t
   }
   if (CL > 1) cl_wait();
 
