@@ -421,7 +421,8 @@ def run_ours(args):
                              "alpha 10), odd segmentation (c1 .2, c2 .8, alpha 20, tau 1), 128x128 subdomains, "
                              f"{INNER} inner", "pixels": bt.pixels(), "ms_per_outer": ms_b,
                  "value": bt.pixels() * INNER / (ms_b * 1e-3) / 1e6, "unit": UNIT,
-                 "launch": "one CUDA graph per 4 outer iterations (2 kernels per outer iteration)"}
+                 "launch": "one CUDA graph per 4 outer iterations (2 kernels per outer iteration: batched multiplier "
+                           "update, persistent clusters over the (image, subdomain) work list)"}
         bt.close()
         del fs
 

@@ -237,7 +237,9 @@ int dd_tv_energy_noalloc(const float* u_dev, const float* f_dev, const uint8_t* 
  * the subdomain size, the number of inner iterations and the initial inner steps, and
  * advance by the same number of outer iterations.  One outer iteration of the whole
  * batch is two kernel launches (multiplier update of every interface of every image,
- * then the local solves of every subdomain of every image), replayed as a CUDA graph.
+ * then the local solves of every subdomain of every image: by default a persistent
+ * kernel whose clusters walk the batch's work list of (image, subdomain) pairs with
+ * each image's fidelity and parameters), replayed as a CUDA graph.
  * Image sides must be multiples of the subdomain side (128).  Results are bit-identical
  * to solving each image alone with the same parameters. */
 typedef struct dd_tv_batch dd_tv_batch;
@@ -254,7 +256,9 @@ typedef struct {
   int tile;               /* subdomain side; 128 is the only value supported             */
   int inner_iters;        /* 1..DD_TV_MAX_INNER                                        */
   double tau0, sigma0;    /* initial inner steps (Section 5: 10 and 1/80)               */
-  int variant;            /* hardware mapping of a subdomain: 0 or 1 (see dd_tv_params)  */
+  int variant;            /* 0: persistent clusters over the batch's work list (default);
+                             1, 2: one cluster per subdomain, 256 / 512 threads; the
+                             results do not depend on it                              */
 } dd_tv_batch_params;
 
 /* Validates and allocates the batch (images[n], n >= 1); *out = NULL on error. */

@@ -1172,10 +1172,44 @@ struct PaLayout {
   static constexpr size_t BYTES = sizeof(float) * MB + 16;
 };
 
+// Sources of the subdomains a persistent cluster iterates over: every tile of one
+// image (fidelity fixed at compile time), or the work list of a batch of images
+// (image, tile) with the fidelity, parameters and coefficients of each image.
+template <int V>
+struct FidC {
+  static constexpr int value = V;
+};
+
+struct OneImageTiles {
+  const LocalArgs& A;
+  __device__ int count() const { return A.g.NR * A.g.NC; }
+  __device__ int inner() const { return A.K; }
+  __device__ int image(int) const { return 0; }
+  __device__ const LocalArgs& args(int) const { return A; }
+  __device__ int local(int t) const { return t; }
+  __device__ int fid(int) const { return -1; }
+  __device__ Strips out(int) const { return A.out; }
+  __device__ int* err() const { return A.err; }
+};
+
+struct BatchTiles {
+  const BatchArgs& B;
+  int total;
+  __device__ int count() const { return total; }
+  __device__ int inner() const { return B.args[0].K; }
+  __device__ int image(int t) const { return B.tile_img[t]; }
+  __device__ const LocalArgs& args(int t) const { return B.args[B.tile_img[t]]; }
+  __device__ int local(int t) const { return t - B.tile_base[B.tile_img[t]]; }
+  __device__ int fid(int t) const { return B.fid[B.tile_img[t]]; }
+  __device__ Strips out(int t) const { return B.strips[2 * B.tile_img[t] + B.write_set]; }
+  __device__ int* err() const { return B.args[0].err; }
+};
+
 // PK: the inner loop works on packed pairs of rows (r, r + R/2) with `*.f32x2`
-// arithmetic (same bits as the scalar loop; the clamps stay scalar).
-template <int R, int TR, int CL, int FID, bool MASK, bool PK>
-__device__ __forceinline__ void fused_pa_body(const LocalArgs& A, const int first, const int stride) {
+// arithmetic (same bits as the scalar loop; the clamps stay scalar).  FIX >= 0: the
+// fidelity of every tile (one image); FIX < 0: each tile's own (a batch).
+template <int R, int TR, int CL, bool MASK, bool PK, int FIX, class Src>
+__device__ __forceinline__ void fused_pa_run(const Src& S, const int first, const int stride) {
   using L = FullLayout<R, TR>;
   using P = PaLayout<R, TR>;
   constexpr int BW = L::BW, BAND = L::BAND, NT = P::NT;
@@ -1193,16 +1227,13 @@ __device__ __forceinline__ void fused_pa_body(const LocalArgs& A, const int firs
   const uint32_t mbU = smem_addr(smem + P::MB);
   const uint32_t mbQ = mbU + 8;
 
-  const Grid g = A.g;
-  const int T = g.NR * g.NC;
+  const int T = S.count();
   const int rank = (int)blockIdx.x;
   const int j = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * BW + j;
   const int lr0 = ty * R;
   const int i0 = rank * BAND + lr0;
-  const int W2 = g.W + g.NC;
-  const float tau = A.tau;
-  const int K = A.K;
+  const int K = S.inner();
   const bool last_row_here = rank == CL - 1 && ty == TR - 1;
   const bool push_down = ty == TR - 1 && rank + 1 < CL;
   const bool push_up = ty == 0 && rank > 0;
@@ -1223,7 +1254,12 @@ __device__ __forceinline__ void fused_pa_body(const LocalArgs& A, const int firs
     mbar_init(mbQ, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int q = tid; q < 8 * min(K, L::kMaxSmemCoef); q += NT) sCo[q] = reinterpret_cast<const float*>(A.coef)[q];
+  int cur_img = -1;  // image whose coefficients are in sCo
+  if constexpr (FIX >= 0) {  // one image: its coefficients once
+    const LocalArgs& A0 = S.args(0);
+    for (int q = tid; q < 8 * min(K, L::kMaxSmemCoef); q += NT) sCo[q] = reinterpret_cast<const float*>(A0.coef)[q];
+    cur_img = 0;
+  }
   if (rank == 0) sU[1 + j] = 0.f;  // u = 0 above every tile's first row
   if (j == 0) sU[0] = 0.f;
   __syncthreads();
@@ -1234,7 +1270,11 @@ __device__ __forceinline__ void fused_pa_body(const LocalArgs& A, const int firs
   cluster_wait();
 
   auto prefetch = [&](int t) {
-    const int a = t / g.NC, b = t - a * g.NC;
+    const LocalArgs& A = S.args(t);
+    const Grid g = A.g;
+    const int W2 = g.W + g.NC;
+    const int lt = S.local(t);
+    const int a = lt / g.NC, b = lt - a * g.NC;
     const int r0 = a * 128, c0 = b * 128, gj = c0 + j;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -1281,18 +1321,31 @@ __device__ __forceinline__ void fused_pa_body(const LocalArgs& A, const int firs
   if (first < T) prefetch(first);
 
   for (int t = first; t < T; t += stride) {
-    const int a = t / g.NC, b = t - a * g.NC;
+    const int img = S.image(t);
+    const LocalArgs& A = S.args(t);
+    const Grid g = A.g;
+    const int W2 = g.W + g.NC;
+    const float tau = A.tau;
+    const Strips out = S.out(t);
+    const int lt = S.local(t);
+    const int a = lt / g.NC, b = lt - a * g.NC;
     const int r0 = a * 128, c0 = b * 128, gj = c0 + j;
     const bool s_top = a > 0, s_bot = a + 1 < g.NR, s_lft = b > 0, s_rgt = b + 1 < g.NC;
     const float lim_left = (j == 0 && !s_lft) ? 0.f : 1.f;
     const float lim_top = (i0 == 0 && !s_top) ? 0.f : 1.f;
     const bool right_lane = s_rgt && j < R;
-    float u[R], p1[R], p2[R], h1[R], h2[R], q1[R];
-    uint32_t in_d = 0;
-    float pB = 0.f, hB = 0.f;
 
     cp_async_wait_all();
     __syncthreads();  // staging landed; the previous subdomain's shared arrays are free
+    if (FIX < 0 && img != cur_img) {  // a batch: made visible by the barrier after the unpack
+      for (int q = tid; q < 8 * min(K, L::kMaxSmemCoef); q += NT) sCo[q] = reinterpret_cast<const float*>(A.coef)[q];
+      cur_img = img;
+    }
+    auto tile_body = [&](auto fidc) {
+    constexpr int FID = decltype(fidc)::value;
+    float u[R], p1[R], p2[R], h1[R], h2[R], q1[R];
+    uint32_t in_d = 0;
+    float pB = 0.f, hB = 0.f;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       u[r] = stg[(0 * R + r) * NT + tid];
@@ -1494,31 +1547,48 @@ __device__ __forceinline__ void fused_pa_body(const LocalArgs& A, const int firs
       A.P1[(size_t)(gi + a) * g.W + gj] = p1[r];
       A.P2[(size_t)gi * W2 + gj + b] = p2[r];
     }
-    if (i0 == 0 && s_top) A.out.ST[(size_t)(a - 1) * g.W + gj] = p1[0];
+    if (i0 == 0 && s_top) out.ST[(size_t)(a - 1) * g.W + gj] = p1[0];
     if (j == 0 && s_lft) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) A.out.SL[(size_t)(b - 1) * g.H + r0 + i0 + r] = p2[r];
+      for (int r = 0; r < R; ++r) out.SL[(size_t)(b - 1) * g.H + r0 + i0 + r] = p2[r];
     }
     if (last_row_here && s_bot) {
       A.P1[(size_t)(r0 + 128 + a) * g.W + gj] = pB;
-      A.out.SB[(size_t)a * g.W + gj] = pB;
+      out.SB[(size_t)a * g.W + gj] = pB;
     }
     if (right_lane) {
       const int gi = r0 + i0 + j;
       const float pr = sPR[lr0 + j];
       A.P2[(size_t)gi * W2 + c0 + 128 + b] = pr;
-      A.out.SR[(size_t)b * g.H + gi] = pr;
+      out.SR[(size_t)b * g.H + gi] = pr;
+    }
+    };  // tile_body
+    if constexpr (FIX >= 0) {
+      tile_body(FidC<FIX>{});
+    } else {
+      switch (S.fid(t)) {
+        case FID_L2: tile_body(FidC<FID_L2>{}); break;
+        case FID_L1: tile_body(FidC<FID_L1>{}); break;
+        default: tile_body(FidC<FID_SEG>{}); break;
+      }
     }
   }
   cp_async_wait_all();
   cluster_arrive<true>();  // no CTA leaves while a neighbour may still write into it
   cluster_wait();
-  if (timed_out) atomicOr(A.err, 1);
+  if (timed_out) atomicOr(S.err(), 1);
 }
 
 template <int R, int TR, int CL, int MINB, int FID, bool MASK, bool PK>
 __global__ void __launch_bounds__(128 * TR, MINB) k_fused_pa(const LocalArgs A) {
-  fused_pa_body<R, TR, CL, FID, MASK, PK>(A, blockIdx.y, gridDim.y);
+  fused_pa_run<R, TR, CL, MASK, PK, FID>(OneImageTiles{A}, blockIdx.y, gridDim.y);
+}
+
+// Persistent kernel over the work list of a batch: cluster c runs tiles c, c + C, ...
+// of the batch, each with its image's fidelity, parameters and coefficients.
+template <int R, int TR, int CL, int MINB, bool PK>
+__global__ void __launch_bounds__(128 * TR, MINB) k_fused_pa_batch(const BatchArgs B, int total) {
+  fused_pa_run<R, TR, CL, false, PK, -1>(BatchTiles{B, total}, blockIdx.y, gridDim.y);
 }
 
 struct Config {
@@ -1730,6 +1800,63 @@ cudaError_t prepare_pa() {
   return prepare_pa_one<R, TR, CL, MINB, FID_SEG, false, PK>();
 }
 
+// persistent batch kernel: clusters resident at once (per device), launch
+template <int R, int TR, int CL, int MINB, bool PK>
+int& pa_batch_clusters(int dev) {
+  static int n[64] = {0};
+  return n[dev & 63];
+}
+
+template <int R, int TR, int CL, int MINB, bool PK>
+cudaError_t prepare_pa_batch() {
+  using P = PaLayout<R, TR>;
+  auto kern = k_fused_pa_batch<R, TR, CL, MINB, PK>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::BYTES);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL, 1024, 1);
+  cfg.blockDim = dim3(128, TR, 1);
+  cfg.dynamicSmemBytes = P::BYTES;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  pa_batch_clusters<R, TR, CL, MINB, PK>(dev) = n;
+  return cudaSuccess;
+}
+
+template <int R, int TR, int CL, int MINB, bool PK>
+cudaError_t launch_pa_batch(const BatchArgs& B, int total_tiles, cudaStream_t st) {
+  using P = PaLayout<R, TR>;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int nc = pa_batch_clusters<R, TR, CL, MINB, PK>(dev);
+  if (nc <= 0 || nc > total_tiles) nc = total_tiles;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL, nc, 1);
+  cfg.blockDim = dim3(128, TR, 1);
+  cfg.dynamicSmemBytes = P::BYTES;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_fused_pa_batch<R, TR, CL, MINB, PK>, B, total_tiles);
+}
+
 template <int R, int TR, int CL, int MINB, int FID, bool MASK>
 cudaError_t prepare_async_one() {
   using AL = AsyncLayout<R, TR>;
@@ -1850,6 +1977,7 @@ cudaError_t fused_prepare() {
   if ((e = prepare_pa<4, 4, 8, 2, true>()) != cudaSuccess) return e;
   if ((e = prepare_pa<16, 1, 8, 2, true>()) != cudaSuccess) return e;
   if ((e = prepare_pa<8, 2, 8, 3, true>()) != cudaSuccess) return e;
+  if ((e = prepare_pa_batch<8, 2, 8, 2, true>()) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_fused_async_batch<8, 2, 8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)AsyncLayout<8, 2>::BYTES)) != cudaSuccess)
     return e;
@@ -1858,8 +1986,9 @@ cudaError_t fused_prepare() {
 }
 
 cudaError_t launch_fused_batch(const BatchArgs& B, int total_tiles, int variant, cudaStream_t st) {
-  if (variant == 1) return launch_async_batch<8, 4, 4, 1>(B, total_tiles, st);
-  return launch_async_batch<8, 2, 8, 2>(B, total_tiles, st);
+  if (variant == 1) return launch_async_batch<8, 2, 8, 2>(B, total_tiles, st);
+  if (variant == 2) return launch_async_batch<8, 4, 4, 1>(B, total_tiles, st);
+  return launch_pa_batch<8, 2, 8, 2, true>(B, total_tiles, st);
 }
 
 cudaError_t launch_fused_local(const LocalArgs& a, int fid, int variant, cudaStream_t st) {
