@@ -424,6 +424,18 @@ def run_ours(args):
                  "launch": "one CUDA graph per 4 outer iterations (2 kernels per outer iteration: batched multiplier "
                            "update, persistent clusters over the (image, subdomain) work list)"}
         bt.close()
+        if not args.no_tune:
+            # inner-iteration count and mapping of the batch by time until every image
+            # reaches relative energy error 1e-4 (J* per image from a long batched run)
+            from paper_1901_00682_gb300 import autotune
+            jr = autotune.batch_reference_energies(ims, fs, inner=20, outer=2000, stream=stream)
+            rb = autotune.tune_batch(ims, fs, tol=1e-4, j_ref=jr, inners=(5, 10, 20), variants=(0,),
+                                     max_outer=3000, stream=stream)
+            bb = rb.best
+            batch["autotuned"] = {"inner_iters": bb.inner, "variant": bb.variant, "device_ms_to_tol": bb.ms,
+                                  "outer_iters": bb.outer, "reached": bb.reached, "tol": 1e-4,
+                                  "j_ref": "lowest energy of a 2000-outer batched run (K = 20) per image",
+                                  "trials": rb.table()}
         del fs
 
     adjoint = None

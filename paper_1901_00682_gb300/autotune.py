@@ -115,6 +115,67 @@ def tune(f, problem, tol=1e-4, j_ref=None, tiles=(64, 128), inners=(5, 10, 20), 
     return TuneResult(best, trials, j_ref, tol)
 
 
+def batch_reference_energies(images, fs, inner=20, outer=2000, variant=0, stream=None):
+    """Lowest energy of every image of a batch over a long batched run (upper bounds
+    of the images' J*).  images: dicts as for _lib.Batch; fs: device tensors."""
+    b = L.Batch(images, inner_iters=inner, variant=variant, stream=stream)
+    b.load(fs)
+    best = [math.inf] * len(images)
+    step = max(outer // 20, 1)
+    for _ in range(0, outer, step):
+        b.iterate(step)
+        for i in range(len(images)):
+            best[i] = min(best[i], b.energy(i))
+    b.close()
+    return best
+
+
+def _batch_trial(images, fs, inner, variant, j_ref, tol, max_outer, check_every, stream):
+    """Device time (CUDA events around the outer iterations only) until every image's
+    relative energy error (J - J*)/|J*| is <= tol, checked every check_every outer
+    iterations; the batch advances all images together."""
+    import torch
+    b = L.Batch(images, inner_iters=inner, variant=variant, stream=stream)
+    st = torch.cuda.current_stream() if stream is None else stream
+    b.load(fs)
+    b.iterate(4)                      # warm-up: graph capture
+    b.load(fs)
+    done, ms, worst = 0, 0.0, math.inf
+    while done < max_outer:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        b.iterate(check_every)
+        e1.record(st)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        done += check_every
+        worst = max((b.energy(i) - j_ref[i]) / abs(j_ref[i]) for i in range(len(images)))
+        if worst <= tol:
+            break
+    b.close()
+    reached = worst <= tol
+    return Trial(128, inner, variant, ms if reached else math.inf, done, worst, reached)
+
+
+def tune_batch(images, fs, tol=1e-4, j_ref=None, inners=(5, 10, 20), variants=(0,), max_outer=3000,
+               check_every=10, stream=None, solve_fn=None):
+    """Chooses the inner-iteration count K and the hardware mapping of a batched solve
+    (subdomain side 128) by the measured device time until every image of the batch
+    reaches relative energy error tol.  j_ref: per-image J* (estimated by
+    batch_reference_energies when None).  solve_fn(inner, variant, j_ref) -> Trial
+    replaces the GPU measurement (host-side tests)."""
+    if j_ref is None and solve_fn is None:
+        j_ref = batch_reference_energies(images, fs, stream=stream)
+    trials = []
+    for inner in inners:
+        for v in variants:
+            if solve_fn is not None:
+                trials.append(solve_fn(inner, v, j_ref))
+            else:
+                trials.append(_batch_trial(images, fs, inner, v, j_ref, tol, max_outer, check_every, stream))
+    return TuneResult(pick_best(trials), trials, j_ref, tol)
+
+
 def time_variants(f, problem, sub_rows, sub_cols, variants, inner=10, outer=100, warmup=8, stream=None):
     """Average device time of one outer iteration (CUDA-graph replay, CUDA events on
     the solver's stream) for each hardware mapping; f is a device tensor."""

@@ -61,3 +61,33 @@ def test_tuned_configuration_reaches_tolerance():
                       outer_iters=b.outer)
     u, _, _ = L.Solver(p).solve_host(f)
     assert (oracle.energy(pr, u.astype(np.float64), f.astype(np.float64)) - jstar) / jstar <= 1.01e-4
+
+
+def test_tune_batch_with_injected_measurement():
+    def fake(inner, variant, j_ref):
+        ms = {5: 30.0, 10: 25.0, 20: 32.0}[inner] + (5.0 if variant == 1 else 0.0)
+        return at.Trial(128, inner, variant, ms, 600 // inner, 8e-5, True)
+
+    r = at.tune_batch([dict(height=128, width=128)], None, j_ref=[1.0], inners=(5, 10, 20), variants=(0, 1),
+                      solve_fn=fake)
+    assert (r.best.inner, r.best.variant) == (10, 0)
+    assert len(r.trials) == 6 and all(t.tile == 128 for t in r.trials)
+
+
+@pytest.mark.gpu
+def test_tuned_batch_reaches_tolerance():
+    """A small mixed batch: the tuned K reaches the tolerance on every image, against
+    J* estimated by a long batched run."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import synth
+    ims = []
+    for k, (h, w, fid) in enumerate([(256, 256, "l2"), (128, 256, "seg"), (256, 128, "l2")]):
+        f, _ = synth.rof_image(h, w, 8, 0.05, 40 + k)
+        ims.append(dict(height=h, width=w, fidelity=fid, alpha=10.0 if fid == "l2" else 20.0,
+                        c1=0.2 if fid == "seg" else 0.0, c2=0.8 if fid == "seg" else 0.0, f=f))
+    fs = [torch.from_numpy(m["f"]).cuda() for m in ims]
+    jr = at.batch_reference_energies(ims, fs, inner=20, outer=1500)
+    r = at.tune_batch(ims, fs, tol=1e-3, j_ref=jr, inners=(5, 10), variants=(0,), max_outer=1500)
+    assert r.best.reached and r.best.rel_err <= 1e-3
