@@ -1172,24 +1172,355 @@ struct PaLayout {
   static constexpr size_t BYTES = sizeof(float) * MB + 16;
 };
 
-// Sources of the subdomains a persistent cluster iterates over: every tile of one
-// image (fidelity fixed at compile time), or the work list of a batch of images
-// (image, tile) with the fidelity, parameters and coefficients of each image.
+// PK: the inner loop works on packed pairs of rows (r, r + R/2) with `*.f32x2`
+// arithmetic (same bits as the scalar loop; the clamps stay scalar).
+template <int R, int TR, int CL, int FID, bool MASK, bool PK>
+__device__ __forceinline__ void fused_pa_body(const LocalArgs& A, const int first, const int stride) {
+  using L = FullLayout<R, TR>;
+  using P = PaLayout<R, TR>;
+  constexpr int BW = L::BW, BAND = L::BAND, NT = P::NT;
+  static_assert(CL * BAND == 128 && CL > 1, "a cluster of CTAs covers the 128 rows of a tile");
+  extern __shared__ __align__(16) float smem[];
+  float* sU = smem + L::U;
+  float* sQ2 = smem + L::Q2;
+  float* sQ1 = smem + L::Q1;
+  float* sF = smem + L::F;
+  float* sPR = smem + L::PR;
+  float* sHR = smem + L::HR;
+  float* sCo = smem + L::CO;
+  float* stg = smem + P::ST;
+  float* stx = smem + P::SX;
+  const uint32_t mbU = smem_addr(smem + P::MB);
+  const uint32_t mbQ = mbU + 8;
+
+  const Grid g = A.g;
+  const int T = g.NR * g.NC;
+  const int rank = (int)blockIdx.x;
+  const int j = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * BW + j;
+  const int lr0 = ty * R;
+  const int i0 = rank * BAND + lr0;
+  const int W2 = g.W + g.NC;
+  const float tau = A.tau;
+  const int K = A.K;
+  const bool last_row_here = rank == CL - 1 && ty == TR - 1;
+  const bool push_down = ty == TR - 1 && rank + 1 < CL;
+  const bool push_up = ty == 0 && rank > 0;
+  const bool need_uh = ty == 0 && rank > 0;
+  const bool need_qh = ty == TR - 1 && rank + 1 < CL;
+  constexpr uint32_t kHaloBytes = 4 * BW;
+  uint32_t remote_u = 0, remote_q1 = 0, remote_mbU = 0, remote_mbQ = 0;
+  if (push_down) {
+    remote_u = map_rank(smem_addr(sU + 1 + j), rank + 1);
+    remote_mbU = map_rank(mbU, rank + 1);
+  }
+  if (push_up) {
+    remote_q1 = map_rank(smem_addr(sQ1 + TR * BW + j), rank - 1);
+    remote_mbQ = map_rank(mbQ, rank - 1);
+  }
+  if (tid == 0) {
+    mbar_init(mbU, 1);
+    mbar_init(mbQ, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int q = tid; q < 8 * min(K, L::kMaxSmemCoef); q += NT) sCo[q] = reinterpret_cast<const float*>(A.coef)[q];
+  if (rank == 0) sU[1 + j] = 0.f;  // u = 0 above every tile's first row
+  if (j == 0) sU[0] = 0.f;
+  __syncthreads();
+  // arm the first phase of each halo barrier this CTA consumes
+  if (need_uh && j == 0) mbar_arrive_expect_tx(mbU, kHaloBytes);
+  if (need_qh && j == 0) mbar_arrive_expect_tx(mbQ, kHaloBytes);
+  cluster_arrive<true>();  // barriers initialised and armed everywhere before any halo is sent
+  cluster_wait();
+
+  auto prefetch = [&](int t) {
+    const int a = t / g.NC, b = t - a * g.NC;
+    const int r0 = a * 128, c0 = b * 128, gj = c0 + j;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int gi = r0 + i0 + r;
+      cp_async4(stg + (0 * R + r) * NT + tid, A.u + (size_t)gi * g.W + gj);
+      cp_async4(stg + (1 * R + r) * NT + tid, A.f + (size_t)gi * g.W + gj);
+      cp_async4(stg + (2 * R + r) * NT + tid, A.P1 + (size_t)(gi + a) * g.W + gj);
+      cp_async4(stg + (3 * R + r) * NT + tid, A.P2 + (size_t)gi * W2 + gj + b);
+    }
+    if (i0 == 0 && a > 0) cp_async4(stx + 0 * NT + tid, A.lamh + (size_t)(a - 1) * g.W + gj);
+    if (last_row_here && a + 1 < g.NR) {
+      cp_async4(stx + 1 * NT + tid, A.P1 + (size_t)(r0 + 128 + a) * g.W + gj);
+      cp_async4(stx + 2 * NT + tid, A.lamh + (size_t)a * g.W + gj);
+    }
+    if (j == 0 && b > 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) cp_async4(stx + (3 + r) * NT + tid, A.lamv + (size_t)(b - 1) * g.H + r0 + i0 + r);
+    }
+    if (j < R && b + 1 < g.NC) {
+      const int gi = r0 + i0 + j;
+      cp_async4(stx + (3 + R) * NT + tid, A.P2 + (size_t)gi * W2 + c0 + 128 + b);
+      cp_async4(stx + (4 + R) * NT + tid, A.lamv + (size_t)b * g.H + gi);
+    }
+    if (need_qh) cp_async4(stx + (5 + R) * NT + tid, A.P1 + (size_t)(r0 + i0 + R + a) * g.W + gj);
+    cp_async_commit();
+  };
+
+  bool timed_out = false;
+  uint32_t phU = 0, phQ = 0;  // index of the next phase of mbU / mbQ this CTA waits for
+  auto wait_u = [&]() {
+    if (!mbar_wait(mbU, phU & 1)) timed_out = true;
+    ++phU;
+    if (j == 0) mbar_arrive_expect_tx(mbU, kHaloBytes);  // arm the next phase
+  };
+  auto wait_q = [&]() {
+    if (!mbar_wait(mbQ, phQ & 1)) timed_out = true;
+    ++phQ;
+    if (j == 0) mbar_arrive_expect_tx(mbQ, kHaloBytes);
+  };
+
+  float* sUr = sU + (lr0 + 1) * L::US + j + 1;
+  float* sQ2r = sQ2 + lr0 * L::QS + j;
+  const float* sFr = sF + lr0 * BW + j;
+  if (first < T) prefetch(first);
+
+  for (int t = first; t < T; t += stride) {
+    const int a = t / g.NC, b = t - a * g.NC;
+    const int r0 = a * 128, c0 = b * 128, gj = c0 + j;
+    const bool s_top = a > 0, s_bot = a + 1 < g.NR, s_lft = b > 0, s_rgt = b + 1 < g.NC;
+    const float lim_left = (j == 0 && !s_lft) ? 0.f : 1.f;
+    const float lim_top = (i0 == 0 && !s_top) ? 0.f : 1.f;
+    const bool right_lane = s_rgt && j < R;
+    float u[R], p1[R], p2[R], h1[R], h2[R], q1[R];
+    uint32_t in_d = 0;
+    float pB = 0.f, hB = 0.f;
+
+    cp_async_wait_all();
+    __syncthreads();  // staging landed; the previous subdomain's shared arrays are free
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      u[r] = stg[(0 * R + r) * NT + tid];
+      float fv = stg[(1 * R + r) * NT + tid];
+      if (FID == FID_SEG) fv = (fv - A.c1) * (fv - A.c1) - (fv - A.c2) * (fv - A.c2);
+      sF[(lr0 + r) * BW + j] = fv;
+      if (MASK && A.mask[(size_t)(r0 + i0 + r) * g.W + gj]) in_d |= 1u << r;
+      p1[r] = stg[(2 * R + r) * NT + tid];
+      p2[r] = stg[(3 * R + r) * NT + tid];
+      h1[r] = p1[r];
+      h2[r] = p2[r];
+      q1[r] = p1[r];
+      sQ2[(lr0 + r) * L::QS + j] = p2[r];
+      sU[(lr0 + r + 1) * L::US] = 0.f;
+    }
+    if (i0 == 0 && s_top) h1[0] = phat_t(p1[0], stx[0 * NT + tid], tau);
+    if (j == 0 && s_lft) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) h2[r] = phat_t(p2[r], stx[(3 + r) * NT + tid], tau);
+    }
+    if (last_row_here) {
+      if (s_bot) {
+        pB = stx[1 * NT + tid];
+        hB = phat_s(pB, stx[2 * NT + tid], tau);
+      }
+      sQ1[TR * BW + j] = pB;
+    }
+    if (need_qh) sQ1[TR * BW + j] = stx[(5 + R) * NT + tid];  // first row of the band below
+    if (j < R) {
+      float pr = 0.f, hr = 0.f;
+      if (s_rgt) {
+        pr = stx[(3 + R) * NT + tid];
+        hr = phat_s(pr, stx[(4 + R) * NT + tid], tau);
+      }
+      sPR[lr0 + j] = pr;
+      sHR[lr0 + j] = hr;
+      sQ2[(lr0 + j) * L::QS + 128] = pr;
+    }
+    sQ1[ty * BW + j] = q1[0];
+    __syncthreads();  // staging consumed by every thread
+    if (t + stride < T) prefetch(t + stride);
+
+    if constexpr (PK) {
+      constexpr int H2 = R / 2;
+      static_assert(R % 2 == 0, "rows are paired");
+      f32x2 U[H2], P1v[H2], P2v[H2], H1v[H2], H2v[H2], Q1v[H2];
+#pragma unroll
+      for (int i = 0; i < H2; ++i) {
+        U[i] = pk2(u[i], u[i + H2]);
+        P1v[i] = pk2(p1[i], p1[i + H2]);
+        P2v[i] = pk2(p2[i], p2[i + H2]);
+        H1v[i] = pk2(h1[i], h1[i + H2]);
+        H2v[i] = pk2(h2[i], h2[i + H2]);
+        Q1v[i] = pk2(q1[i], q1[i + H2]);
+      }
+      for (int k = 0; k < K; ++k) {
+        Coef c;
+        if (k < L::kMaxSmemCoef) {
+          const float4 ca = *reinterpret_cast<const float4*>(sCo + 8 * k);
+          const float4 cb = *reinterpret_cast<const float4*>(sCo + 8 * k + 4);
+          c = Coef{ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+        } else {
+          c = A.coef[k];
+        }
+        const f32x2 SIG = pk2(c.sig, c.sig), UA = pk2(c.ua, c.ua), UB = pk2(c.ub, c.ub);
+        const f32x2 PA = pk2(c.pa, c.pa), PC = pk2(c.pc, c.pc), PB = pk2(c.pb, c.pb), TH = pk2(c.th, c.th);
+        if (need_qh && k > 0) wait_q();  // pbar1 halo of iteration k-1
+        // u-step on row pairs; the pair holding the band's last row first
+#pragma unroll
+        for (int ii = 0; ii < H2; ++ii) {
+          const int i = (ii + H2 - 1) % H2;
+          const f32x2 below = i + 1 < H2 ? Q1v[i + 1] : pk2(hi2(Q1v[0]), sQ1[(ty + 1) * BW + j]);
+          const f32x2 left = pk2(sQ2r[i * L::QS], sQ2r[(i + H2) * L::QS]);
+          const f32x2 right = pk2(sQ2r[i * L::QS + 1], sQ2r[(i + H2) * L::QS + 1]);
+          const f32x2 d = sub2(add2(sub2(below, Q1v[i]), right), left);  // div_px
+          const f32x2 fg = pk2(sFr[i * BW], sFr[(i + H2) * BW]);
+          const f32x2 ub = fma2(SIG, d, U[i]);
+          f32x2 un;
+          if (FID == FID_L2) {
+            un = fma2(UB, fg, mul2(UA, ub));
+            if (MASK)
+              un = pk2(((in_d >> i) & 1u) ? lo2(ub) : lo2(un), ((in_d >> (i + H2)) & 1u) ? hi2(ub) : hi2(un));
+          } else {
+            un = pk2(prox_ubar<FID>(lo2(ub), lo2(fg), MASK && ((in_d >> i) & 1u), c),
+                     prox_ubar<FID>(hi2(ub), hi2(fg), MASK && ((in_d >> (i + H2)) & 1u), c));
+          }
+          U[i] = un;
+          sUr[i * L::US] = lo2(un);
+          sUr[(i + H2) * L::US] = hi2(un);
+          if (ii == 0 && push_down) st_async_f32(remote_u, hi2(un), remote_mbU);
+        }
+        __syncthreads();
+        if (need_uh) wait_u();  // u halo of iteration k
+        // p-step on row pairs; the pair holding the band's first row first
+#pragma unroll
+        for (int i = 0; i < H2; ++i) {
+          const f32x2 above = i > 0 ? U[i - 1] : pk2(sUr[-L::US], lo2(U[H2 - 1]));
+          const f32x2 leftu = pk2(sUr[i * L::US - 1], sUr[(i + H2) * L::US - 1]);
+          {
+            const f32x2 tt = fma2(PC, sub2(U[i], above), fma2(PA, P1v[i], mul2(PB, H1v[i])));  // p_target
+            const float l0 = i == 0 ? lim_top : 1.f;
+            const f32x2 pn = pk2(fminf(fmaxf(lo2(tt), -l0), l0), fminf(fmaxf(hi2(tt), -1.f), 1.f));
+            Q1v[i] = fma2(TH, sub2(pn, P1v[i]), pn);
+            P1v[i] = pn;
+          }
+          {
+            const f32x2 tt = fma2(PC, sub2(U[i], leftu), fma2(PA, P2v[i], mul2(PB, H2v[i])));
+            const f32x2 pn = pk2(fminf(fmaxf(lo2(tt), -lim_left), lim_left),
+                                 fminf(fmaxf(hi2(tt), -lim_left), lim_left));
+            const f32x2 q2 = fma2(TH, sub2(pn, P2v[i]), pn);
+            P2v[i] = pn;
+            sQ2r[i * L::QS] = lo2(q2);
+            sQ2r[(i + H2) * L::QS] = hi2(q2);
+          }
+          if (i == 0) {
+            const float q10 = lo2(Q1v[0]);
+            sQ1[ty * BW + j] = q10;
+            if (push_up) st_async_f32(remote_q1, q10, remote_mbQ);
+          }
+        }
+        if (last_row_here && s_bot) {
+          float qB;
+          p_update(pB, qB, -hi2(U[H2 - 1]), hB, c);
+          sQ1[TR * BW + j] = qB;
+        }
+        if (right_lane) {
+          const int lr = lr0 + j;
+          float pr = sPR[lr], qr;
+          p_update(pr, qr, -sU[(lr + 1) * L::US + 128], sHR[lr], c);
+          sPR[lr] = pr;
+          sQ2[lr * L::QS + 128] = qr;
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int i = 0; i < H2; ++i) {
+        u[i] = lo2(U[i]);
+        u[i + H2] = hi2(U[i]);
+        p1[i] = lo2(P1v[i]);
+        p1[i + H2] = hi2(P1v[i]);
+        p2[i] = lo2(P2v[i]);
+        p2[i + H2] = hi2(P2v[i]);
+      }
+    } else {
+      for (int k = 0; k < K; ++k) {
+        Coef c;
+        if (k < L::kMaxSmemCoef) {
+          const float4 ca = *reinterpret_cast<const float4*>(sCo + 8 * k);
+          const float4 cb = *reinterpret_cast<const float4*>(sCo + 8 * k + 4);
+          c = Coef{ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+        } else {
+          c = A.coef[k];
+        }
+        if (need_qh && k > 0) wait_q();  // pbar1 halo of iteration k-1
+  #pragma unroll
+        for (int rr = 0; rr < R; ++rr) {
+          const int r = (rr + R - 1) % R;
+          const float below = r + 1 < R ? q1[r + 1] : sQ1[(ty + 1) * BW + j];
+          const float d = div_px(q1[r], below, sQ2r[r * L::QS], sQ2r[r * L::QS + 1]);
+          u[r] = u_update<FID>(u[r], d, sFr[r * BW], MASK && ((in_d >> r) & 1u), c);
+          sUr[r * L::US] = u[r];
+          if (rr == 0 && push_down) st_async_f32(remote_u, u[R - 1], remote_mbU);
+        }
+        __syncthreads();
+        if (need_uh) wait_u();  // u halo of iteration k
+  #pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const float above = r > 0 ? u[r - 1] : sUr[-L::US];
+          p_update_lim(p1[r], q1[r], u[r] - above, h1[r], c, r == 0 ? lim_top : 1.f);
+          float q2;
+          p_update_lim(p2[r], q2, u[r] - sUr[r * L::US - 1], h2[r], c, lim_left);
+          sQ2r[r * L::QS] = q2;
+          if (r == 0) {
+            sQ1[ty * BW + j] = q1[0];
+            if (push_up) st_async_f32(remote_q1, q1[0], remote_mbQ);
+          }
+        }
+        if (last_row_here && s_bot) {
+          float qB;
+          p_update(pB, qB, -u[R - 1], hB, c);
+          sQ1[TR * BW + j] = qB;
+        }
+        if (right_lane) {
+          const int lr = lr0 + j;
+          float pr = sPR[lr], qr;
+          p_update(pr, qr, -sU[(lr + 1) * L::US + 128], sHR[lr], c);
+          sPR[lr] = pr;
+          sQ2[lr * L::QS + 128] = qr;
+        }
+        __syncthreads();
+      }
+    }
+    if (need_qh) wait_q();  // drain the last pbar1 halo (not read)
+
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int gi = r0 + i0 + r;
+      A.u[(size_t)gi * g.W + gj] = u[r];
+      A.P1[(size_t)(gi + a) * g.W + gj] = p1[r];
+      A.P2[(size_t)gi * W2 + gj + b] = p2[r];
+    }
+    if (i0 == 0 && s_top) A.out.ST[(size_t)(a - 1) * g.W + gj] = p1[0];
+    if (j == 0 && s_lft) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) A.out.SL[(size_t)(b - 1) * g.H + r0 + i0 + r] = p2[r];
+    }
+    if (last_row_here && s_bot) {
+      A.P1[(size_t)(r0 + 128 + a) * g.W + gj] = pB;
+      A.out.SB[(size_t)a * g.W + gj] = pB;
+    }
+    if (right_lane) {
+      const int gi = r0 + i0 + j;
+      const float pr = sPR[lr0 + j];
+      A.P2[(size_t)gi * W2 + c0 + 128 + b] = pr;
+      A.out.SR[(size_t)b * g.H + gi] = pr;
+    }
+  }
+  cp_async_wait_all();
+  cluster_arrive<true>();  // no CTA leaves while a neighbour may still write into it
+  cluster_wait();
+  if (timed_out) atomicOr(A.err, 1);
+}
+
+// The batch's work list as the source of the subdomains a persistent cluster iterates
+// over: (image, tile) with the fidelity, parameters and coefficients of each image.
 template <int V>
 struct FidC {
   static constexpr int value = V;
-};
-
-struct OneImageTiles {
-  const LocalArgs& A;
-  __device__ int count() const { return A.g.NR * A.g.NC; }
-  __device__ int inner() const { return A.K; }
-  __device__ int image(int) const { return 0; }
-  __device__ const LocalArgs& args(int) const { return A; }
-  __device__ int local(int t) const { return t; }
-  __device__ int fid(int) const { return -1; }
-  __device__ Strips out(int) const { return A.out; }
-  __device__ int* err() const { return A.err; }
 };
 
 struct BatchTiles {
@@ -1205,10 +1536,12 @@ struct BatchTiles {
   __device__ int* err() const { return B.args[0].err; }
 };
 
-// PK: the inner loop works on packed pairs of rows (r, r + R/2) with `*.f32x2`
-// arithmetic (same bits as the scalar loop; the clamps stay scalar).  FIX >= 0: the
-// fidelity of every tile (one image); FIX < 0: each tile's own (a batch).
-template <int R, int TR, int CL, bool MASK, bool PK, int FIX, class Src>
+// Persistent body over a source of subdomains of several images (the batch): the
+// single-image body above with, per subdomain, the image's geometry, parameters,
+// strips and fidelity (dispatched at run time), and the image's coefficients reloaded
+// into shared memory when the image changes.  (The single-image kernel keeps its own
+// copy of the body: the per-subdomain indirection measured 2 % slower there.)
+template <int R, int TR, int CL, bool MASK, bool PK, class Src>
 __device__ __forceinline__ void fused_pa_run(const Src& S, const int first, const int stride) {
   using L = FullLayout<R, TR>;
   using P = PaLayout<R, TR>;
@@ -1255,11 +1588,6 @@ __device__ __forceinline__ void fused_pa_run(const Src& S, const int first, cons
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   int cur_img = -1;  // image whose coefficients are in sCo
-  if constexpr (FIX >= 0) {  // one image: its coefficients once
-    const LocalArgs& A0 = S.args(0);
-    for (int q = tid; q < 8 * min(K, L::kMaxSmemCoef); q += NT) sCo[q] = reinterpret_cast<const float*>(A0.coef)[q];
-    cur_img = 0;
-  }
   if (rank == 0) sU[1 + j] = 0.f;  // u = 0 above every tile's first row
   if (j == 0) sU[0] = 0.f;
   __syncthreads();
@@ -1326,7 +1654,6 @@ __device__ __forceinline__ void fused_pa_run(const Src& S, const int first, cons
     const Grid g = A.g;
     const int W2 = g.W + g.NC;
     const float tau = A.tau;
-    const Strips out = S.out(t);
     const int lt = S.local(t);
     const int a = lt / g.NC, b = lt - a * g.NC;
     const int r0 = a * 128, c0 = b * 128, gj = c0 + j;
@@ -1337,7 +1664,7 @@ __device__ __forceinline__ void fused_pa_run(const Src& S, const int first, cons
 
     cp_async_wait_all();
     __syncthreads();  // staging landed; the previous subdomain's shared arrays are free
-    if (FIX < 0 && img != cur_img) {  // a batch: made visible by the barrier after the unpack
+    if (img != cur_img) {  // made visible by the barrier after the unpack
       for (int q = tid; q < 8 * min(K, L::kMaxSmemCoef); q += NT) sCo[q] = reinterpret_cast<const float*>(A.coef)[q];
       cur_img = img;
     }
@@ -1547,6 +1874,7 @@ __device__ __forceinline__ void fused_pa_run(const Src& S, const int first, cons
       A.P1[(size_t)(gi + a) * g.W + gj] = p1[r];
       A.P2[(size_t)gi * W2 + gj + b] = p2[r];
     }
+    const Strips out = S.out(t);
     if (i0 == 0 && s_top) out.ST[(size_t)(a - 1) * g.W + gj] = p1[0];
     if (j == 0 && s_lft) {
 #pragma unroll
@@ -1563,14 +1891,10 @@ __device__ __forceinline__ void fused_pa_run(const Src& S, const int first, cons
       out.SR[(size_t)b * g.H + gi] = pr;
     }
     };  // tile_body
-    if constexpr (FIX >= 0) {
-      tile_body(FidC<FIX>{});
-    } else {
-      switch (S.fid(t)) {
-        case FID_L2: tile_body(FidC<FID_L2>{}); break;
-        case FID_L1: tile_body(FidC<FID_L1>{}); break;
-        default: tile_body(FidC<FID_SEG>{}); break;
-      }
+    switch (S.fid(t)) {
+      case FID_L2: tile_body(FidC<FID_L2>{}); break;
+      case FID_L1: tile_body(FidC<FID_L1>{}); break;
+      default: tile_body(FidC<FID_SEG>{}); break;
     }
   }
   cp_async_wait_all();
@@ -1581,14 +1905,14 @@ __device__ __forceinline__ void fused_pa_run(const Src& S, const int first, cons
 
 template <int R, int TR, int CL, int MINB, int FID, bool MASK, bool PK>
 __global__ void __launch_bounds__(128 * TR, MINB) k_fused_pa(const LocalArgs A) {
-  fused_pa_run<R, TR, CL, MASK, PK, FID>(OneImageTiles{A}, blockIdx.y, gridDim.y);
+  fused_pa_body<R, TR, CL, FID, MASK, PK>(A, blockIdx.y, gridDim.y);
 }
 
 // Persistent kernel over the work list of a batch: cluster c runs tiles c, c + C, ...
 // of the batch, each with its image's fidelity, parameters and coefficients.
 template <int R, int TR, int CL, int MINB, bool PK>
 __global__ void __launch_bounds__(128 * TR, MINB) k_fused_pa_batch(const BatchArgs B, int total) {
-  fused_pa_run<R, TR, CL, false, PK, -1>(BatchTiles{B, total}, blockIdx.y, gridDim.y);
+  fused_pa_run<R, TR, CL, false, PK>(BatchTiles{B, total}, blockIdx.y, gridDim.y);
 }
 
 struct Config {
