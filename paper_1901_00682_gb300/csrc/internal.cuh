@@ -114,6 +114,12 @@ int fused_num_variants();
 // Name of the configuration chosen for a tile shape and variant (for reports).
 const char* fused_config_name(int mr, int mc, int variant);
 
+// ---- kernels_fused_ghost.cu
+// Persistent fused local solver with one halo exchange per inner iteration (ghost row
+// above each CTA's band); 128 x 128 tiles only.
+cudaError_t launch_fused_pg(const LocalArgs& a, int fidelity, cudaStream_t st);
+cudaError_t fused_pg_prepare();
+
 // ---- kernels_plain.cu
 // phat = p~ -+ tau lambda on the interface sides, pbar = p~; full arrays.
 cudaError_t launch_plain_phat(const LocalArgs& a, float* Ph1, float* Ph2, float* Pb1, float* Pb2, cudaStream_t st);

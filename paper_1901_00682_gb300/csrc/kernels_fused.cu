@@ -24,78 +24,11 @@
 // cross-SM latency of the cluster barrier hides behind the interior work.  Only
 // warps that wrote to a neighbour arrive with release semantics.
 #include "internal.cuh"
+#include "fused_common.cuh"
 
 namespace ddtv {
 
 namespace {
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint32_t map_rank(uint32_t addr, int rank) {
-  uint32_t out;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(addr), "r"(rank));
-  return out;
-}
-
-__device__ __forceinline__ void st_cluster(uint32_t addr, float v) {
-  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
-}
-
-__device__ __forceinline__ void st_cluster_f64(uint32_t addr, double v) {
-  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
-}
-
-// Packed float32 pairs (sm_100+ `*.f32x2`): one instruction performs the operation on
-// two lanes, each rounded exactly as the scalar instruction, so packed and scalar code
-// give identical bits.
-typedef unsigned long long f32x2;
-
-__device__ __forceinline__ f32x2 pk2(float lo, float hi) {
-  f32x2 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ float lo2(f32x2 v) {
-  float a, b;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-  return a;
-}
-__device__ __forceinline__ float hi2(f32x2 v) {
-  float a, b;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-  return b;
-}
-__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
-  f32x2 r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
-  f32x2 r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
-  f32x2 r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-// a * b + c, one rounding per lane (fmaf)
-__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
-  f32x2 r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
-}
-
-template <bool RELEASE>
-__device__ __forceinline__ void cluster_arrive() {
-  if (RELEASE)
-    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-  else
-    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
 template <int BW, int R, int TR>
 struct SmemLayout {
@@ -113,14 +46,6 @@ struct SmemLayout {
   static constexpr int FLOATS = HR + BAND;
   static constexpr size_t BYTES = sizeof(float) * FLOATS;
 };
-
-// p_update with the clamp to [-lim, lim]; lim = 0 pins an inactive dof at 0
-__device__ __forceinline__ void p_update_lim(float& p, float& pbar, float du, float phat, const Coef& c, float lim) {
-  const float t = p_target(p, du, phat, c);
-  const float pn = fminf(fmaxf(t, -lim), lim);
-  pbar = fmaf(c.th, pn - p, pn);
-  p = pn;
-}
 
 // ADAPT: adaptive inner stopping (Section 5, eq. stop_inner1).  Every thread sums
 // (p^{k+1} - p^k)^2 and (p^{k+1})^2 over the tile dofs it owns (float32), the CTA adds
@@ -391,30 +316,6 @@ __global__ void __launch_bounds__(BW* TR, (BW * TR <= 256 ? 2 : 1)) k_fused(cons
   }
 }
 
-// ---------------------------------------------------------------------------
-// Full-tile kernel: every subdomain is exactly 128 x 128 (the partition of the
-// benchmark workloads).  Same arithmetic as k_fused, without any per-pixel
-// boundary test: the band's halo rows live in the shared arrays (row 0 of sU is
-// the row above the band, row TR of sQ1 the row below it), the tile's bottom side
-// is the "row below" of the last CTA, and the right side's dofs are updated by
-// lanes 0..R-1 of each thread row's first warp (one dof per lane).
-template <int R, int TR>
-struct FullLayout {
-  static constexpr int BW = 128;
-  static constexpr int BAND = TR * R;
-  static constexpr int US = BW + 1;                    // u row stride; index 0 = zero pad
-  static constexpr int QS = BW + 1;                    // pbar2 row stride; index 128 = right side
-  static constexpr int U = 0;                          // (BAND + 1) x US: row 0 = row above the band
-  static constexpr int Q2 = U + (BAND + 1) * US;       // BAND x QS
-  static constexpr int Q1 = Q2 + BAND * QS;            // (TR + 1) x BW: first-row pbar1 per thread row; row TR = below
-  static constexpr int F = Q1 + (TR + 1) * BW;         // BAND x BW
-  static constexpr int PR = F + BAND * BW;             // BAND right-side p
-  static constexpr int HR = PR + BAND;                 // BAND right-side phat
-  static constexpr int CO = (HR + BAND + 3) & ~3;      // kMaxSmemCoef x 8 coefficients (16-byte aligned)
-  static constexpr int FLOATS = CO + 8 * 64;
-  static constexpr size_t BYTES = sizeof(float) * FLOATS;
-  static constexpr int kMaxSmemCoef = 64;
-};
 
 template <int R, int TR, int CL, int MINB, int FID, bool MASK>
 __global__ void __launch_bounds__(128 * TR, MINB) k_fused_full(const LocalArgs A) {
@@ -613,46 +514,6 @@ __global__ void __launch_bounds__(128 * TR, MINB) k_fused_full(const LocalArgs A
 // feeds).
 // A waiting warp sleeps in mbarrier.try_wait until the phase completes or the hint
 // (ns) runs out; kWaitLimit rounds of it bound the wait at about one second.
-constexpr unsigned kWaitLimit = 1000;
-constexpr unsigned kSuspendHintNs = 1000000;
-
-__device__ __forceinline__ void mbar_init(uint32_t addr, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_local(uint32_t addr) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(addr)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(addr), "r"(parity), "r"(kSuspendHintNs)
-      : "memory");
-  return ok != 0;
-}
-
-// bounded wait; returns false (and the caller records the timeout) when the limit runs out
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
-  for (unsigned it = 0; it < kWaitLimit; ++it)
-    if (mbar_try_wait(addr, parity)) return true;
-  return false;
-}
-
-__device__ __forceinline__ void st_cluster_v4(uint32_t addr, float4 v) {
-  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z),
-               "f"(v.w)
-               : "memory");
-}
-
 template <int R, int NW>
 struct WrLayout {
   static constexpr int BAND = NW * R;
@@ -896,18 +757,6 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_fused_wr(const LocalArgs A) {
 // producer's stores bring the byte count to zero.  A producer cannot run a phase
 // ahead of its consumer (its next halo row depends on the consumer's previous one),
 // so the single halo buffers are never overwritten while being read.
-__device__ __forceinline__ void st_async_f32(uint32_t remote_addr, float v, uint32_t remote_mbar) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(remote_addr),
-               "r"(__float_as_uint(v)), "r"(remote_mbar)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t addr, uint32_t bytes) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.release.cta.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(addr),
-               "r"(bytes)
-               : "memory");
-}
-
 template <int R, int TR>
 struct AsyncLayout {
   using F = FullLayout<R, TR>;
@@ -1140,12 +989,6 @@ __global__ void __launch_bounds__(128 * TR, MINB) k_fused_async_batch(const Batc
   }
 }
 
-__device__ __forceinline__ void cp_async4(float* dst_smem, const float* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst_smem)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
 // ---------------------------------------------------------------------------
 // Persistent asynchronous kernel.  The arithmetic and on-chip mapping of
 // k_fused_async, but each cluster loops over subdomains t = cluster, cluster + C, ...
@@ -1160,17 +1003,6 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // warps that send a CTA's halos are the ones that drain (wait for) the last halo they
 // receive, which their neighbour sends only after reading the halo they sent before,
 // so no halo buffer is overwritten while it may still be read.
-template <int R, int TR>
-struct PaLayout {
-  using F = FullLayout<R, TR>;
-  static constexpr int NT = 128 * TR;
-  static constexpr int ST = (F::FLOATS + 3) & ~3;          // staging [field][r][thread]: u, f, p1, p2
-  static constexpr int SX = ST + 4 * R * NT;               // extras [x][thread]
-  static constexpr int NX = 6 + R;                          // lamh above, P1 bottom, lamh below, lamv left[R], P2 right,
-                                                            // lamv right, initial pbar1 of the row below the band
-  static constexpr int MB = (SX + NX * NT + 1) & ~1;        // mbU, mbQ
-  static constexpr size_t BYTES = sizeof(float) * MB + 16;
-};
 
 // PK: the inner loop works on packed pairs of rows (r, r + R/2) with `*.f32x2`
 // arithmetic (same bits as the scalar loop; the clamps stay scalar).
@@ -1929,7 +1761,7 @@ constexpr Config kConfigs[] = {
     {128, 8, 4, 4, "bw128_r8_tr4_cl4"},    // class 2, variant 1: 512 threads, 1 CTA/SM
     {128, 16, 2, 4, "bw128_r16_tr2_cl4"},  // class 2, variant 2: 256 threads, 16 rows/thread
 };
-constexpr int kNumVariants = 10;
+constexpr int kNumVariants = 11;
 
 template <int BW, int R, int TR, int CL, int FID, bool MASK, bool ADAPT>
 cudaError_t launch_one(const LocalArgs& a, cudaStream_t st) {
@@ -2302,6 +2134,7 @@ cudaError_t fused_prepare() {
   if ((e = prepare_pa<16, 1, 8, 2, true>()) != cudaSuccess) return e;
   if ((e = prepare_pa<8, 2, 8, 3, true>()) != cudaSuccess) return e;
   if ((e = prepare_pa_batch<8, 2, 8, 2, true>()) != cudaSuccess) return e;
+  if ((e = fused_pg_prepare()) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_fused_async_batch<8, 2, 8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)AsyncLayout<8, 2>::BYTES)) != cudaSuccess)
     return e;
@@ -2331,6 +2164,7 @@ cudaError_t launch_fused_local(const LocalArgs& a, int fid, int variant, cudaStr
       case 7: return launch_pa<4, 4, 8, 2, true>(a, fid, st);   // packed, 4 rows per thread: 512 threads, 2 CTAs/SM
       case 8: return launch_pa<16, 1, 8, 2, true>(a, fid, st);  // packed, 16 rows per thread: 128 threads
       case 9: return launch_pa<8, 2, 8, 3, true>(a, fid, st);   // variant 0 at 3 CTAs per SM (85 registers)
+      case 10: return launch_fused_pg(a, fid, st);              // one halo exchange per inner iteration
       default: return cudaErrorInvalidValue;
     }
   }

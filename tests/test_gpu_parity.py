@@ -225,7 +225,7 @@ def test_fused_variants_bitwise_identical(H, W, NR, NC):
     L = _gpu()
     f, _ = synth.rof_image(H, W, 12, 0.1, 12)
     outs = []
-    for v in range(10):
+    for v in range(11):
         _, g, _, _ = _run_gpu(f, None, 7, sub_rows=NR, sub_cols=NC, alpha=8.0, variant=v)
         outs.append(g)
     for g in outs[1:]:
