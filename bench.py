@@ -69,6 +69,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, pg=None, device=None) -> float:
+    """The maximum of x over all ranks of the process group (x itself without one)."""
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(work_per_rank: float, world: int, seconds: float) -> float:
+    """Units of all ranks per second, in millions (every rank does the same work; the
+    job takes as long as its slowest rank)."""
+    return world * work_per_rank / seconds / 1e6
+
+
 class ClockSampler:
     """Samples nvidia-smi SM clocks and throttle reasons in the background."""
 
@@ -301,13 +317,9 @@ def run_ours(args):
     ms_total = e0.elapsed_time(e1)
     prof_ms, prof_n = s.profile_read()
     s.set_profiling(False)
-    t_max = ms_total
-    if pg:
-        tt = torch.tensor([ms_total], device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(ms_total, pg, dev)
     work = H * W * INNER * args.steps
-    value = world * work / (t_max * 1e-3) / 1e6
+    value = whole_job_rate(work, world, t_max * 1e-3)
 
     # ---- roofline of the fused local solver (dominant kernel)
     local_avg_ms = prof_ms["local"] / max(prof_n["local"], 1)
@@ -355,12 +367,8 @@ def run_ours(args):
         pg.barrier()
     t = time.perf_counter()
     _, st_e2e, _ = se.solve_host(f_pin.numpy(), None, u_pin.numpy())
-    dt_e2e = time.perf_counter() - t
-    if pg:
-        tt = torch.tensor([dt_e2e], device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        dt_e2e = float(tt.item())
-    e2e = {"value": world * work / dt_e2e / 1e6, "unit": UNIT,
+    dt_e2e = max_over_ranks(time.perf_counter() - t, pg, dev)
+    e2e = {"value": whole_job_rate(work, world, dt_e2e), "unit": UNIT,
            "h2d_bytes_per_step": 4 * H * W / args.steps,
            "d2h_bytes_per_step": (4 * H * W + 16 * (args.steps // ENERGY_EVERY)) / args.steps,
            "call": "dd_tv_solve(host f, host u), one call of K outer iterations with the energy check "
