@@ -36,6 +36,34 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Run by every thread of the last block to finish: adds the n block partial pairs in a
+// fixed order (thread t takes pairs t, t + blockDim, ...; warps, then the warp sums in
+// order), so the result does not depend on scheduling and the partials' load latency
+// is paid once per thread instead of once per block.
+__device__ __forceinline__ void finish_pairs(const double* partials, int n, double* sj, double* sd, double& tj,
+                                             double& td) {
+  double a = 0.0, b = 0.0;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    a += ((volatile const double*)partials)[2 * q];
+    b += ((volatile const double*)partials)[2 * q + 1];
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();  // the block's sj / sd are free again
+  if (lane == 0) {
+    sj[wid] = a;
+    sd[wid] = b;
+  }
+  __syncthreads();
+  tj = td = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      tj += sj[w];
+      td += sd[w];
+    }
+}
+
 // averaged global dof of the horizontal edge above pixel row i (0 < i < H), column j
 __device__ __forceinline__ float avg_p1(const Grid& g, const float* P1, int i, int j) {
   const int a = part_of(i, g.H, g.NR);
@@ -109,16 +137,93 @@ __global__ void __launch_bounds__(kBlock) k_energy(Grid g, int fid, float alpha,
     last = ticket == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
+  if (last) {
     __threadfence();
-    double tj = 0.0, td = 0.0;
-    for (int q = 0; q < (int)gridDim.x; ++q) {
-      tj += ((volatile double*)partials)[2 * q];
-      td += ((volatile double*)partials)[2 * q + 1];
+    double tj, td;
+    finish_pairs(partials, (int)gridDim.x, sj, sd, tj, td);
+    if (threadIdx.x == 0) {
+      out[0] = tj;
+      out[1] = dual ? td : -INFINITY;
+      *counter = 0u;  // ready for the next call
     }
-    out[0] = tj;
-    out[1] = dual ? td : -INFINITY;
-    *counter = 0u;  // ready for the next call
+  }
+}
+
+// Primal energy only, rows of W % 4 == 0 pixels with 16-byte aligned u, f (and mask
+// rows 4-byte aligned): block b takes rows b, b + gridDim.x, ...; a thread takes float4
+// chunks of a row (4 pixels: their fidelity terms, the 3 differences inside the chunk,
+// the one to the next chunk and the 4 to the row below).  Same compensated sums and
+// fixed-order combination as k_energy, without a division per pixel.
+template <int FID, bool MASK>
+__global__ void __launch_bounds__(kBlock) k_energy_rows(int H, int W, float alpha, float c1, float c2,
+                                                         const float* __restrict__ u, const float* __restrict__ f,
+                                                         const uint8_t* __restrict__ mask,
+                                                         double* __restrict__ partials,
+                                                         unsigned int* __restrict__ counter, double* __restrict__ out) {
+  Kahan sF, sT;
+  const int W4 = W >> 2;
+  for (int i = blockIdx.x; i < H; i += gridDim.x) {
+    const float4* ur = reinterpret_cast<const float4*>(u + (size_t)i * W);
+    const float4* fr = reinterpret_cast<const float4*>(f + (size_t)i * W);
+    const bool below = i + 1 < H;
+    const float4* ub = reinterpret_cast<const float4*>(u + (size_t)(i + 1) * W);
+    for (int q = threadIdx.x; q < W4; q += blockDim.x) {
+      const float4 a = ur[q];
+      const float4 fv = fr[q];
+      const float nx = q + 1 < W4 ? u[(size_t)i * W + 4 * q + 4] : a.w;
+      const float4 d = below ? ub[q] : a;
+      uchar4 m4 = make_uchar4(0, 0, 0, 0);
+      if (MASK) m4 = reinterpret_cast<const uchar4*>(mask + (size_t)i * W)[q];
+      // the chunk's terms are added in float (at most 8 non-negative terms), then once
+      // into the compensated sums: short dependency chains, loads of the next chunk overlap
+      const float th = (fabsf(a.y - a.x) + fabsf(a.z - a.y)) + (fabsf(a.w - a.z) + fabsf(nx - a.w));
+      const float tv = (fabsf(d.x - a.x) + fabsf(d.y - a.y)) + (fabsf(d.z - a.z) + fabsf(d.w - a.w));
+      sT.add(th + tv);
+      const float uu[4] = {a.x, a.y, a.z, a.w}, ff[4] = {fv.x, fv.y, fv.z, fv.w};
+      const unsigned char mm[4] = {m4.x, m4.y, m4.z, m4.w};
+      float fe[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (FID == FID_SEG) {
+          const float gv = (ff[e] - c1) * (ff[e] - c1) - (ff[e] - c2) * (ff[e] - c2);
+          fe[e] = uu[e] * gv;
+        } else if (!(MASK && mm[e])) {
+          const float r = uu[e] - ff[e];
+          fe[e] = FID == FID_L2 ? 0.5f * r * r : fabsf(r);
+        } else {
+          fe[e] = 0.f;
+        }
+      }
+      sF.add((fe[0] + fe[1]) + (fe[2] + fe[3]));
+    }
+  }
+  double vJ = (double)alpha * ((double)sF.s - (double)sF.c) + ((double)sT.s - (double)sT.c);
+  vJ = warp_sum(vJ);
+  __shared__ double sj[kBlock / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sj[wid] = vJ;
+  __syncthreads();
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    double bj = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) bj += sj[w];
+    partials[2 * blockIdx.x] = bj;
+    partials[2 * blockIdx.x + 1] = 0.0;
+    __threadfence();
+    const unsigned int ticket = atomicAdd(counter, 1u);
+    last = ticket == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    __shared__ double sd[kBlock / 32];
+    double tj, td;
+    finish_pairs(partials, (int)gridDim.x, sj, sd, tj, td);
+    if (threadIdx.x == 0) {
+      out[0] = tj;
+      out[1] = -INFINITY;
+      *counter = 0u;  // ready for the next call
+    }
   }
 }
 
@@ -129,7 +234,18 @@ int reduce_partials_count() { return 2 * kBlocks; }
 cudaError_t launch_energy(const Grid& g, int fid, float alpha, float c1, float c2, const float* u, const float* f,
                           const uint8_t* mask, const float* P1, const float* P2, double* partials,
                           unsigned int* counter, double* out, cudaStream_t st) {
-  k_energy<<<kBlocks, kBlock, 0, st>>>(g, fid, alpha, c1, c2, u, f, mask, P1, P2, partials, counter, out);
+  const bool rows = P1 == nullptr && g.W % 4 == 0 && ((uintptr_t)u % 16 == 0) && ((uintptr_t)f % 16 == 0) &&
+                    (mask == nullptr || (uintptr_t)mask % 4 == 0);
+  if (!rows) {
+    k_energy<<<kBlocks, kBlock, 0, st>>>(g, fid, alpha, c1, c2, u, f, mask, P1, P2, partials, counter, out);
+    return cudaGetLastError();
+  }
+  const int nb = g.H < kBlocks ? g.H : kBlocks;
+#define ROWS(F, M) k_energy_rows<F, M><<<nb, kBlock, 0, st>>>(g.H, g.W, alpha, c1, c2, u, f, mask, partials, counter, out)
+  if (fid == FID_SEG) ROWS(FID_SEG, false);
+  else if (fid == FID_L1) { if (mask) ROWS(FID_L1, true); else ROWS(FID_L1, false); }
+  else { if (mask) ROWS(FID_L2, true); else ROWS(FID_L2, false); }
+#undef ROWS
   return cudaGetLastError();
 }
 
