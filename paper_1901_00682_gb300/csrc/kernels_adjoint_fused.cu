@@ -16,6 +16,7 @@
 // column to the right, the p-step's adjoint (a_t of every dof) by the row above and the
 // column to the left; halo rows cross CTAs through DSMEM stores ordered by the split
 // cluster barrier, as in the forward kernel.
+#include "fused_common.cuh"
 #include "internal.cuh"
 
 namespace ddtv {
@@ -464,6 +465,399 @@ __global__ void __launch_bounds__(BW* TR, MINB) k_adj_fused(const LocalArgs A, c
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same reverse pass for subdomains of exactly 128 x 128 pixels, with the halo
+// exchange of the asynchronous forward kernel (k_fused_async): a halo row is stored
+// into the neighbour CTA with st.async and counted on an mbarrier there; only the
+// warps that read a halo wait for it (bounded), and no cluster barrier runs inside the
+// loops.  The reverse iteration has the forward's pattern, so the two barriers go on
+// counting phases: the u halo (forward u, reverse Ad) travels down, the pbar1 halo
+// (forward pbar1, reverse a_t of the first row) travels up.  No per-pixel validity test
+// is needed: every thread owns 8 rows of one column.  Arithmetic and operation order
+// are those of k_adj_fused (same bits).
+template <int R, int TR>
+struct AdjFullLayout {
+  using F = FullLayout<R, TR>;
+  static constexpr int XR = F::FLOATS;             // BAND: right-side adjoint of phat
+  static constexpr int MB = (XR + TR * R + 1) & ~1;  // mbU, mbQ
+  static constexpr size_t BYTES = sizeof(float) * MB + 16;
+  static constexpr size_t tape_floats(int K) { return (size_t)K * (R + 1) * (128 * TR); }
+};
+
+template <int R, int TR, int CL, int MINB, int FID, bool MASK>
+__global__ void __launch_bounds__(128 * TR, MINB) k_adj_full(const LocalArgs A, const AdjArgs Z) {
+  using L = FullLayout<R, TR>;
+  using AL = AdjFullLayout<R, TR>;
+  constexpr int BW = L::BW, BAND = L::BAND, NT = BW * TR;
+  static_assert(CL * BAND == 128 && CL > 1, "a cluster of CTAs covers the 128 rows of a tile");
+  static_assert(R <= 8, "pass-bit word layout");
+  extern __shared__ __align__(16) float smem[];
+  float* sU = smem + L::U;
+  float* sQ2 = smem + L::Q2;
+  float* sQ1 = smem + L::Q1;
+  float* sF = smem + L::F;
+  float* sPR = smem + L::PR;
+  float* sHR = smem + L::HR;
+  float* sCo = smem + L::CO;
+  float* sXR = smem + AL::XR;
+  const uint32_t mbU = smem_addr(smem + AL::MB);
+  const uint32_t mbQ = mbU + 8;
+
+  const Grid g = A.g;
+  const int K = A.K;
+  const int rank = (int)blockIdx.x;
+  const int b = blockIdx.y, a = blockIdx.z;
+  const int r0 = a * 128, c0 = b * 128;
+  const bool s_top = a > 0, s_bot = a + 1 < g.NR, s_lft = b > 0, s_rgt = b + 1 < g.NC;
+  const int j = threadIdx.x, ty = threadIdx.y, tid = ty * BW + j;
+  const int lr0 = ty * R;
+  const int i0 = rank * BAND + lr0;
+  const int W2 = g.W + g.NC;
+  const int gj = c0 + j;
+  const float tau = A.tau;
+  const float lim_left = (j == 0 && !s_lft) ? 0.f : 1.f;
+  const float lim_top = (i0 == 0 && !s_top) ? 0.f : 1.f;
+  const bool last_row_here = rank == CL - 1 && ty == TR - 1;
+  const bool push_down = ty == TR - 1 && rank + 1 < CL;  // last row -> u / Ad halo of rank + 1
+  const bool push_up = ty == 0 && rank > 0;              // first row -> pbar1 / a_t halo of rank - 1
+  const bool need_uh = push_up, need_qh = push_down;
+  const bool right_lane = s_rgt && j < R;                // the right side of band row lr0 + j
+  constexpr uint32_t kHaloBytes = 4 * BW;
+  float* tapeU = Z.tape + ((size_t)(a * g.NC + b) * CL + rank) * AL::tape_floats(K);
+  uint32_t* tapeM = reinterpret_cast<uint32_t*>(tapeU + (size_t)K * R * NT);
+  uint32_t remote_u = 0, remote_q1 = 0, remote_mbU = 0, remote_mbQ = 0;
+  if (push_down) {
+    remote_u = map_rank(smem_addr(sU + 1 + j), rank + 1);
+    remote_mbU = map_rank(mbU, rank + 1);
+  }
+  if (push_up) {
+    remote_q1 = map_rank(smem_addr(sQ1 + TR * BW + j), rank - 1);
+    remote_mbQ = map_rank(mbQ, rank - 1);
+  }
+  if (tid == 0) {
+    mbar_init(mbU, 1);
+    mbar_init(mbQ, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  bool timed_out = false;
+  uint32_t phU = 0, phQ = 0;
+  auto wait_u = [&]() {
+    if (j == 0) mbar_arrive_expect_tx(mbU, kHaloBytes);
+    if (!mbar_wait(mbU, phU & 1u)) timed_out = true;
+    ++phU;
+  };
+  auto wait_q = [&]() {
+    if (j == 0) mbar_arrive_expect_tx(mbQ, kHaloBytes);
+    if (!mbar_wait(mbQ, phQ & 1u)) timed_out = true;
+    ++phQ;
+  };
+
+  float u[R], p1[R], p2[R], h1[R], h2[R], q1[R];
+  uint32_t in_d = 0;
+  float pB = 0.f, hB = 0.f;
+  for (int q = tid; q < 8 * min(K, L::kMaxSmemCoef); q += NT) sCo[q] = reinterpret_cast<const float*>(A.coef)[q];
+  if (rank == 0) sU[1 + j] = 0.f;  // nothing above the tile's first row
+  if (j == 0) sU[0] = 0.f;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int gi = r0 + i0 + r;
+    const size_t px = (size_t)gi * g.W + gj;
+    u[r] = A.u[px];
+    float fv = A.f[px];
+    if (FID == FID_SEG) fv = (fv - A.c1) * (fv - A.c1) - (fv - A.c2) * (fv - A.c2);
+    sF[(lr0 + r) * BW + j] = fv;
+    if (MASK && A.mask[px]) in_d |= 1u << r;
+    p1[r] = A.P1[(size_t)(gi + a) * g.W + gj];
+    p2[r] = A.P2[(size_t)gi * W2 + gj + b];
+    h1[r] = p1[r];
+    h2[r] = p2[r];
+    q1[r] = p1[r];
+    sQ2[(lr0 + r) * L::QS + j] = p2[r];
+    sU[(lr0 + r + 1) * L::US] = 0.f;
+  }
+  if (i0 == 0 && s_top) h1[0] = phat_t(p1[0], A.lamh[(size_t)(a - 1) * g.W + gj], tau);
+  if (j == 0 && s_lft) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) h2[r] = phat_t(p2[r], A.lamv[(size_t)(b - 1) * g.H + r0 + i0 + r], tau);
+  }
+  if (last_row_here) {
+    if (s_bot) {
+      pB = A.P1[(size_t)(r0 + 128 + a) * g.W + gj];
+      hB = phat_s(pB, A.lamh[(size_t)a * g.W + gj], tau);
+    }
+    sQ1[TR * BW + j] = pB;
+  }
+  if (j < R) {
+    float pr = 0.f, hr = 0.f;
+    if (s_rgt) {
+      const int gi = r0 + i0 + j;
+      pr = A.P2[(size_t)gi * W2 + c0 + 128 + b];
+      hr = phat_s(pr, A.lamv[(size_t)b * g.H + gi], tau);
+    }
+    sPR[lr0 + j] = pr;
+    sHR[lr0 + j] = hr;
+    sQ2[(lr0 + j) * L::QS + 128] = pr;
+  }
+  sQ1[ty * BW + j] = q1[0];
+  __syncthreads();
+  cluster_arrive<true>();  // barriers initialised everywhere before any halo is sent
+  cluster_wait();
+  if (push_up) st_cluster(remote_q1, q1[0]);  // the initial pbar1 halo, ordered by the barrier
+  cluster_arrive<true>();
+  cluster_wait();
+
+  float* sUr = sU + (lr0 + 1) * L::US + j + 1;
+  float* sQ2r = sQ2 + lr0 * L::QS + j;
+  const float* sFr = sF + lr0 * BW + j;
+
+  // ---- forward: K inner iterations, recording the tape
+  for (int k = 0; k < K; ++k) {
+    Coef c;
+    if (k < L::kMaxSmemCoef) {
+      const float4 ca = *reinterpret_cast<const float4*>(sCo + 8 * k);
+      const float4 cb = *reinterpret_cast<const float4*>(sCo + 8 * k + 4);
+      c = Coef{ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+    } else {
+      c = A.coef[k];
+    }
+    float* tU = tapeU + (size_t)k * R * NT;
+    if (need_qh && k > 0) wait_q();
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+      const int r = (rr + R - 1) % R;
+      const float below = r + 1 < R ? q1[r + 1] : sQ1[(ty + 1) * BW + j];
+      const float d = div_px(q1[r], below, sQ2r[r * L::QS], sQ2r[r * L::QS + 1]);
+      const float ub = fmaf(c.sig, d, u[r]);
+      tU[r * NT + tid] = ub;
+      u[r] = prox_ubar<FID>(ub, sFr[r * BW], MASK && ((in_d >> r) & 1u), c);
+      sUr[r * L::US] = u[r];
+      if (rr == 0 && push_down) st_async_f32(remote_u, u[R - 1], remote_mbU);
+    }
+    __syncthreads();
+    if (need_uh) wait_u();
+    uint32_t bits = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float above = r > 0 ? u[r - 1] : sUr[-L::US];
+      bits |= p_step_bit(p1[r], q1[r], u[r] - above, h1[r], c, r == 0 ? lim_top : 1.f) << r;
+      float q2;
+      bits |= p_step_bit(p2[r], q2, u[r] - sUr[r * L::US - 1], h2[r], c, lim_left) << (8 + r);
+      sQ2r[r * L::QS] = q2;
+      if (r == 0) {
+        sQ1[ty * BW + j] = q1[0];
+        if (push_up) st_async_f32(remote_q1, q1[0], remote_mbQ);
+      }
+    }
+    if (last_row_here && s_bot) {
+      float qB;
+      bits |= p_step_bit(pB, qB, -u[R - 1], hB, c, 1.f) << 16;
+      sQ1[TR * BW + j] = qB;
+    }
+    if (right_lane) {
+      const int lr = lr0 + j;
+      float pr = sPR[lr], qr;
+      bits |= p_step_bit(pr, qr, -sU[(lr + 1) * L::US + 128], sHR[lr], c, 1.f) << 17;
+      sPR[lr] = pr;
+      sQ2[lr * L::QS + 128] = qr;
+    }
+    tapeM[(size_t)k * NT + tid] = bits;
+    __syncthreads();
+  }
+  if (need_qh) wait_q();  // the last forward pbar1 halo is not read
+  // every forward halo has landed everywhere before the reverse sends its first ones
+  // (otherwise two pushes into the same halo buffer could be in flight at once)
+  cluster_arrive<true>();
+  cluster_wait();
+
+  // ---- reverse (registers: adjoints of u, p1, p2, pbar1, pbar2, phat1, phat2 and of
+  // the bottom side; the right side's in sPR / sHR / sXR, handled by lane j for band
+  // row lr0 + j; sU = Ad with row 0 the halo from above, sQ2 = a_t of the p2 dofs and
+  // the right side, sQ1 = a_t of each thread row's first p1 row, row TR from below)
+  float Au[R], AP1[R], AP2[R], AQ1[R], AQ2[R], AH1[R], AH2[R], Afr[R];
+  float APB = 0.f, AQB = 0.f, AHB = 0.f;
+  double acc = 0.0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int gi = r0 + i0 + r;
+    Au[r] = Z.Au[(size_t)gi * g.W + gj];
+    AP1[r] = Z.AP1[(size_t)(gi + a) * g.W + gj];
+    AP2[r] = Z.AP2[(size_t)gi * W2 + gj + b];
+    AQ1[r] = AQ2[r] = AH1[r] = AH2[r] = Afr[r] = 0.f;
+  }
+  if (last_row_here && s_bot) APB = Z.AP1[(size_t)(r0 + 128 + a) * g.W + gj];
+  if (right_lane) {
+    sPR[lr0 + j] = Z.AP2[(size_t)(r0 + i0 + j) * W2 + c0 + 128 + b];
+    sHR[lr0 + j] = 0.f;
+    sXR[lr0 + j] = 0.f;
+  }
+  {
+    const Coef c = A.coef[K - 1];
+    const float opq = 1.0f + c.th;
+    const uint32_t bits = tapeM[(size_t)(K - 1) * NT + tid];
+#pragma unroll
+    for (int r = 0; r < R; ++r) sQ2r[r * L::QS] = ((bits >> (8 + r)) & 1u) ? AP2[r] + opq * AQ2[r] : 0.0f;
+    if (j < R) {
+      const int lr = lr0 + j;
+      sQ2[lr * L::QS + 128] = (right_lane && ((bits >> 17) & 1u)) ? sPR[lr] + opq * sHR[lr] : 0.0f;
+    }
+    const float at10 = (bits & 1u) ? AP1[0] + opq * AQ1[0] : 0.0f;
+    sQ1[ty * BW + j] = at10;
+    if (last_row_here) sQ1[TR * BW + j] = (s_bot && ((bits >> 16) & 1u)) ? APB + opq * AQB : 0.0f;
+    __syncthreads();  // the forward's reads of sQ1 / sQ2 are over in this CTA
+    if (push_up) st_async_f32(remote_q1, at10, remote_mbQ);
+  }
+
+  for (int k = K - 1; k >= 0; --k) {
+    const Coef c = A.coef[k];
+    const float opq = 1.0f + c.th;
+    const uint32_t bits = tapeM[(size_t)k * NT + tid];
+    const float* tU = tapeU + (size_t)k * R * NT;
+    float ubk[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) ubk[r] = tU[r * NT + tid];
+    const bool first = k == K - 1, last = k == 0;
+    const uint32_t bn = k > 0 ? tapeM[(size_t)(k - 1) * NT + tid] : 0u;
+    const float opn = k > 0 ? 1.0f + A.coef[k - 1].th : 0.0f;
+    float Ad[R];
+    if (need_qh) wait_q();  // a_t of the first row below, iteration k
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+      const int r = (rr + R - 1) % R;
+      const float at_top = ((bits >> r) & 1u) ? AP1[r] + opq * AQ1[r] : 0.0f;
+      const float at_bot = r + 1 < R ? (((bits >> (r + 1)) & 1u) ? AP1[r + 1] + opq * AQ1[r + 1] : 0.0f)
+                                     : sQ1[(ty + 1) * BW + j];
+      const float at_left = ((bits >> (8 + r)) & 1u) ? AP2[r] + opq * AQ2[r] : 0.0f;
+      const float at_right = sQ2r[r * L::QS + 1];
+      const float dv = div_px(c.pc * at_top, c.pc * at_bot, c.pc * at_left, c.pc * at_right);
+      const float aun = Au[r] - dv;
+      float dub, df, dal;
+      prox_partials_fg<FID>(ubk[r], sFr[r * BW], MASK && ((in_d >> r) & 1u), A.c1, A.c2, c, dub, df, dal);
+      const float aub = dub * aun;
+      Au[r] = aub;
+      Ad[r] = c.sig * aub;
+      sUr[r * L::US] = Ad[r];
+      if (df != 0.0f) Afr[r] += df * aun;
+      acc += (double)dal * (double)aun;
+      if (rr == 0 && push_down) st_async_f32(remote_u, Ad[R - 1], remote_mbU);
+    }
+    __syncthreads();
+    if (need_uh) wait_u();  // Ad of the last row above, iteration k
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float ad_above = r > 0 ? Ad[r - 1] : sUr[-L::US];
+      const float ad_left = sUr[r * L::US - 1];
+      adj_dof_reg(AP1[r], AQ1[r], AH1[r], (bits >> r) & 1u, ad_above - Ad[r], c, opq, first, last);
+      adj_dof_reg(AP2[r], AQ2[r], AH2[r], (bits >> (8 + r)) & 1u, ad_left - Ad[r], c, opq, first, last);
+      if (k > 0) sQ2r[r * L::QS] = ((bn >> (8 + r)) & 1u) ? AP2[r] + opn * AQ2[r] : 0.0f;
+      if (r == 0 && k > 0) {
+        const float at10 = (bn & 1u) ? AP1[0] + opn * AQ1[0] : 0.0f;
+        sQ1[ty * BW + j] = at10;
+        if (push_up) st_async_f32(remote_q1, at10, remote_mbQ);
+      }
+    }
+    if (last_row_here && s_bot) {
+      adj_dof_reg(APB, AQB, AHB, (bits >> 16) & 1u, Ad[R - 1], c, opq, first, last);
+      if (k > 0) sQ1[TR * BW + j] = ((bn >> 16) & 1u) ? APB + opn * AQB : 0.0f;
+    }
+    if (right_lane) {
+      const int lr = lr0 + j;
+      float ap = sPR[lr], aq = sHR[lr], ah = sXR[lr];
+      adj_dof_reg(ap, aq, ah, (bits >> 17) & 1u, sU[(lr + 1) * L::US + 128], c, opq, first, last);
+      sPR[lr] = ap;
+      sHR[lr] = aq;
+      sXR[lr] = ah;
+      if (k > 0) sQ2[lr * L::QS + 128] = ((bn >> 17) & 1u) ? ap + opn * aq : 0.0f;
+    }
+    __syncthreads();
+  }
+  if (timed_out) atomicOr(A.err, 1);
+  cluster_arrive<true>();  // no CTA leaves while a neighbour may still write into it
+  cluster_wait();
+
+  // ---- store: Au, AP (folded), APhat on the subdomain's sides; Af += ; alpha partials
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int gi = r0 + i0 + r;
+    const size_t px = (size_t)gi * g.W + gj;
+    Z.Au[px] = Au[r];
+    if (Afr[r] != 0.0f) Z.Af[px] += Afr[r];
+    const size_t e1 = (size_t)(gi + a) * g.W + gj, e2 = (size_t)gi * W2 + gj + b;
+    if (i0 + r > 0 || s_top) Z.AP1[e1] = AP1[r];
+    if (j > 0 || s_lft) Z.AP2[e2] = AP2[r];
+    if (i0 + r == 0 && s_top) Z.APh1[e1] = AH1[r];
+    if (j == 0 && s_lft) Z.APh2[e2] = AH2[r];
+  }
+  if (last_row_here && s_bot) {
+    const size_t e = (size_t)(r0 + 128 + a) * g.W + gj;
+    Z.AP1[e] = APB;
+    Z.APh1[e] = AHB;
+  }
+  if (right_lane) {
+    const size_t e = (size_t)(r0 + i0 + j) * W2 + c0 + 128 + b;
+    Z.AP2[e] = sPR[lr0 + j];
+    Z.APh2[e] = sXR[lr0 + j];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  __shared__ double sw[NT / 32];
+  if ((tid & 31) == 0) sw[tid >> 5] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < NT / 32; ++w) t += sw[w];
+    Z.Aal[((size_t)a * g.NC + b) * CL + rank] += t;
+  }
+}
+
+template <int R, int TR, int CL, int MINB, int FID, bool MASK>
+cudaError_t launch_adj_full_one(const LocalArgs& a, const AdjArgs& z, cudaStream_t st) {
+  using AL = AdjFullLayout<R, TR>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL, a.g.NC, a.g.NR);
+  cfg.blockDim = dim3(128, TR, 1);
+  cfg.dynamicSmemBytes = AL::BYTES;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_adj_full<R, TR, CL, MINB, FID, MASK>, a, z);
+}
+
+template <int R, int TR, int CL, int MINB>
+cudaError_t launch_adj_full(const LocalArgs& a, const AdjArgs& z, int fid, cudaStream_t st) {
+  const bool m = a.mask != nullptr;
+  switch (fid) {
+    case FID_L2:
+      return m ? launch_adj_full_one<R, TR, CL, MINB, FID_L2, true>(a, z, st)
+               : launch_adj_full_one<R, TR, CL, MINB, FID_L2, false>(a, z, st);
+    case FID_L1:
+      return m ? launch_adj_full_one<R, TR, CL, MINB, FID_L1, true>(a, z, st)
+               : launch_adj_full_one<R, TR, CL, MINB, FID_L1, false>(a, z, st);
+    default: return launch_adj_full_one<R, TR, CL, MINB, FID_SEG, false>(a, z, st);
+  }
+}
+
+template <int R, int TR, int CL, int MINB, int FID, bool MASK>
+cudaError_t prepare_adj_full_one() {
+  using AL = AdjFullLayout<R, TR>;
+  return cudaFuncSetAttribute(k_adj_full<R, TR, CL, MINB, FID, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)AL::BYTES);
+}
+
+template <int R, int TR, int CL, int MINB>
+cudaError_t prepare_adj_full() {
+  cudaError_t e;
+  if ((e = prepare_adj_full_one<R, TR, CL, MINB, FID_L2, false>()) != cudaSuccess) return e;
+  if ((e = prepare_adj_full_one<R, TR, CL, MINB, FID_L2, true>()) != cudaSuccess) return e;
+  if ((e = prepare_adj_full_one<R, TR, CL, MINB, FID_L1, false>()) != cudaSuccess) return e;
+  if ((e = prepare_adj_full_one<R, TR, CL, MINB, FID_L1, true>()) != cudaSuccess) return e;
+  return prepare_adj_full_one<R, TR, CL, MINB, FID_SEG, false>();
+}
+
 template <int BW, int R, int TR, int CL, int MINB, int FID, bool MASK>
 cudaError_t launch_adj_one(const LocalArgs& a, const AdjArgs& z, cudaStream_t st) {
   using L = AdjLayout<BW, R, TR>;
@@ -539,12 +933,15 @@ size_t adj_fused_tape_floats(const Grid& g, int K) {
 
 cudaError_t adj_fused_prepare() {
   cudaError_t e;
+  if ((e = prepare_adj_full<8, 2, 8, 2>()) != cudaSuccess) return e;
   if ((e = prepare_adj_cfg<32, 8, 4, 1, 1>()) != cudaSuccess) return e;
   if ((e = prepare_adj_cfg<64, 8, 8, 1, 1>()) != cudaSuccess) return e;
   return prepare_adj_cfg<128, 8, 2, 8, 2>();
 }
 
 cudaError_t launch_adj_fused(const LocalArgs& a, const AdjArgs& z, int fid, cudaStream_t st) {
+  if (a.g.H == 128 * a.g.NR && a.g.W == 128 * a.g.NC)  // every subdomain exactly 128 x 128
+    return launch_adj_full<8, 2, 8, 2>(a, z, fid, st);
   const int mr = (a.g.H + a.g.NR - 1) / a.g.NR, mc = (a.g.W + a.g.NC - 1) / a.g.NC;
   switch (adj_pick(mr, mc)) {
     case 0: return launch_adj_cfg<32, 8, 4, 1, 1>(a, z, fid, st);
