@@ -339,7 +339,7 @@ def run_ours(args):
     roofline = {
         "bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s", "frac": achieved / smem_peak,
         "traffic": traffic,
-        "kernel": "fused local solver (k_fused_pa: persistent clusters of 8 CTAs x 256 threads, one 128x128 subdomain at a time)",
+        "kernel": "fused local solver (k_fused_mt: persistent clusters of 8 CTAs x 256 threads, one 128x128 subdomain at a time, 2x4 pixel micro-tile per thread)",
         "peak_source": "measured live: ld.shared probe kernel (dd_tv_measure_smem_bandwidth)",
         "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": local_avg_ms,
         "hbm_state_stream": {"bytes_per_launch": 28 * H * W,

@@ -120,6 +120,28 @@ const char* fused_config_name(int mr, int mc, int variant);
 cudaError_t launch_fused_pg(const LocalArgs& a, int fidelity, cudaStream_t st);
 cudaError_t fused_pg_prepare();
 
+// ---- kernels_fused_mt.cu
+// Persistent fused local solver on 2 x 4 micro-tiles (two columns by four rows per
+// thread); 128 x 128 tiles with u, f, P1 16-byte aligned (fused_mt_supported).
+bool fused_mt_supported(const LocalArgs& a);
+cudaError_t launch_fused_mt(const LocalArgs& a, int fidelity, cudaStream_t st);
+cudaError_t fused_mt_prepare();
+
+// ---- kernels_fused_wrow.cu
+// Persistent fused local solver with one warp per pair of rows (named-barrier
+// exchange between adjacent warps, bulk asynchronous copies of the state); 128 x 128
+// tiles with 16-byte aligned rows (fused_wrow_supported).
+bool fused_wrow_supported(const LocalArgs& a);
+cudaError_t launch_fused_wrow(const LocalArgs& a, int fidelity, cudaStream_t st);
+cudaError_t fused_wrow_prepare();
+
+// ---- kernels_fused_ps.cu
+// Persistent fused local solver, column mapping with 16-byte state copies and an
+// out-buffer; 128 x 128 tiles with 16-byte aligned rows (fused_ps_supported).
+bool fused_ps_supported(const LocalArgs& a);
+cudaError_t launch_fused_ps(const LocalArgs& a, int fidelity, cudaStream_t st);
+cudaError_t fused_ps_prepare();
+
 // ---- kernels_plain.cu
 // phat = p~ -+ tau lambda on the interface sides, pbar = p~; full arrays.
 cudaError_t launch_plain_phat(const LocalArgs& a, float* Ph1, float* Ph2, float* Pb1, float* Pb2, cudaStream_t st);

@@ -1761,7 +1761,7 @@ constexpr Config kConfigs[] = {
     {128, 8, 4, 4, "bw128_r8_tr4_cl4"},    // class 2, variant 1: 512 threads, 1 CTA/SM
     {128, 16, 2, 4, "bw128_r16_tr2_cl4"},  // class 2, variant 2: 256 threads, 16 rows/thread
 };
-constexpr int kNumVariants = 11;
+constexpr int kNumVariants = 14;
 
 template <int BW, int R, int TR, int CL, int FID, bool MASK, bool ADAPT>
 cudaError_t launch_one(const LocalArgs& a, cudaStream_t st) {
@@ -2135,6 +2135,9 @@ cudaError_t fused_prepare() {
   if ((e = prepare_pa<8, 2, 8, 3, true>()) != cudaSuccess) return e;
   if ((e = prepare_pa_batch<8, 2, 8, 2, true>()) != cudaSuccess) return e;
   if ((e = fused_pg_prepare()) != cudaSuccess) return e;
+  if ((e = fused_mt_prepare()) != cudaSuccess) return e;
+  if ((e = fused_wrow_prepare()) != cudaSuccess) return e;
+  if ((e = fused_ps_prepare()) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_fused_async_batch<8, 2, 8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)AsyncLayout<8, 2>::BYTES)) != cudaSuccess)
     return e;
@@ -2154,17 +2157,23 @@ cudaError_t launch_fused_local(const LocalArgs& a, int fid, int variant, cudaStr
   if (a.inner_tol2 > 0.0) variant = 0;  // adaptive stopping: the cluster-barrier kernel only
   if (a.inner_tol2 <= 0.0 && a.g.H == 128 * a.g.NR && a.g.W == 128 * a.g.NC) {  // every tile exactly 128 x 128
     switch (variant) {
-      case 0: return launch_pa<8, 2, 8, 2, true>(a, fid, st);   // persistent, async halos, prefetch, packed pairs
+      case 0:  // default: persistent, 2 x 4 micro-tiles, edge exchange only
+        return fused_mt_supported(a) ? launch_fused_mt(a, fid, st) : launch_pa<8, 2, 8, 2, true>(a, fid, st);
       case 1: return launch_async<8, 2, 8, 2>(a, fid, st);      // async halos, one subdomain per cluster
       case 2: return launch_full<8, 4, 4, 1>(a, fid, st);       // cluster barrier per half-step: 512 threads
       case 3: return launch_wr<2, 8, 8, 2>(a, fid, st);         // warp rows, per-warp mbarriers
       case 4: return launch_pa<8, 4, 4, 1, false>(a, fid, st);  // persistent, async halos, prefetch: 512 threads
       case 5: return launch_async<8, 4, 4, 1>(a, fid, st);      // async halos: 512 threads
-      case 6: return launch_pa<8, 2, 8, 2, false>(a, fid, st);  // variant 0 with scalar arithmetic
-      case 7: return launch_pa<4, 4, 8, 2, true>(a, fid, st);   // packed, 4 rows per thread: 512 threads, 2 CTAs/SM
-      case 8: return launch_pa<16, 1, 8, 2, true>(a, fid, st);  // packed, 16 rows per thread: 128 threads
-      case 9: return launch_pa<8, 2, 8, 3, true>(a, fid, st);   // variant 0 at 3 CTAs per SM (85 registers)
+      case 6: return launch_pa<8, 2, 8, 2, false>(a, fid, st);  // variant 11 with scalar arithmetic
+      case 7: return launch_pa<4, 4, 8, 2, true>(a, fid, st);   // variant 11 with 4 rows per thread: 512 threads
+      case 8: return launch_pa<16, 1, 8, 2, true>(a, fid, st);  // variant 11 with 16 rows per thread: 128 threads
+      case 9: return launch_pa<8, 2, 8, 3, true>(a, fid, st);   // variant 11 at 3 CTAs per SM (80 registers)
       case 10: return launch_fused_pg(a, fid, st);              // one halo exchange per inner iteration
+      case 11: return launch_pa<8, 2, 8, 2, true>(a, fid, st);  // persistent column mapping, packed pairs
+      case 12:                                                  // warp per row pair, named barriers, bulk copies
+        return fused_wrow_supported(a) ? launch_fused_wrow(a, fid, st) : launch_pa<8, 2, 8, 2, true>(a, fid, st);
+      case 13:                                                  // variant 11 with 16-byte copies, out-buffer
+        return fused_ps_supported(a) ? launch_fused_ps(a, fid, st) : launch_pa<8, 2, 8, 2, true>(a, fid, st);
       default: return cudaErrorInvalidValue;
     }
   }

@@ -219,13 +219,48 @@ def test_full_size_4096_sampled_parity():
     assert np.abs(g["lamh"] - o.lamh).max() <= 1e-3
 
 
+N_VARIANTS = 14  # hardware mappings of a 128 x 128 subdomain (dd_tv_params.variant)
+
+
+def test_variant_count():
+    L = _gpu()
+    with L.Solver(L.make_params(256, 256, 2, 2, variant=N_VARIANTS - 1)):
+        pass
+    with pytest.raises(L.DDTVError) as e:
+        L.Solver(L.make_params(256, 256, 2, 2, variant=N_VARIANTS))
+    assert e.value.code == L.EINVAL
+
+
+@pytest.mark.parametrize("fid,mask_prob,K", [("l2", 0.2, 10), ("l1", 0.2, 10), ("seg", 0.0, 10), ("l2", 0.0, 70)])
+def test_persistent_variants_bitwise_all_fidelities(fid, mask_prob, K):
+    """The default micro-tile mapping against the column (11), warp-row (12) and
+    16-byte-copy (13) mappings for every fidelity, with and without the inpainting mask,
+    and with more inner iterations than the kernels keep in shared memory (K = 70:
+    coefficients 64.. come from global memory)."""
+    L = _gpu()
+    H, W = 384, 256
+    f, _ = synth.rof_image(H, W, 12, 0.1, 5)
+    mask = None
+    if mask_prob:
+        mask = synth.bernoulli_mask((H, W), mask_prob, np.random.Generator(np.random.PCG64(9)))
+        f = np.where(mask == 1, 0.0, f).astype(np.float32)
+    kw = dict(sub_rows=3, sub_cols=2, fidelity=fid, alpha={"l2": 8.0, "l1": 1.5, "seg": 20.0}[fid],
+              inner_iters=K)
+    if fid == "seg":
+        kw.update(c1=0.2, c2=0.8, tau=1.0)
+    outs = [_run_gpu(f, mask, 5, variant=v, **kw)[1] for v in (0, 11, 12, 13)]
+    for o in outs[1:]:
+        for k in ("u", "P1", "P2", "lamh", "lamv"):
+            assert np.array_equal(outs[0][k], o[k]), k
+
+
 @pytest.mark.parametrize("H,W,NR,NC", [(384, 384, 3, 3), (250, 260, 2, 3), (128, 128, 1, 1), (1024, 1280, 8, 10)])
 def test_fused_variants_bitwise_identical(H, W, NR, NC):
     """Every hardware mapping of a 128x128-class subdomain runs the same arithmetic."""
     L = _gpu()
     f, _ = synth.rof_image(H, W, 12, 0.1, 12)
     outs = []
-    for v in range(11):
+    for v in range(N_VARIANTS):
         _, g, _, _ = _run_gpu(f, None, 7, sub_rows=NR, sub_cols=NC, alpha=8.0, variant=v)
         outs.append(g)
     for g in outs[1:]:
