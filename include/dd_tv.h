@@ -256,9 +256,11 @@ typedef struct {
   int tile;               /* subdomain side; 128 is the only value supported             */
   int inner_iters;        /* 1..DD_TV_MAX_INNER                                        */
   double tau0, sigma0;    /* initial inner steps (Section 5: 10 and 1/80)               */
-  int variant;            /* 0: persistent clusters over the batch's work list (default);
-                             1, 2: one cluster per subdomain, 256 / 512 threads; the
-                             results do not depend on it                              */
+  int variant;            /* 0: persistent clusters over the batch's work list, 2 x 4
+                             pixel micro-tiles per thread (default); 1, 2: one cluster
+                             per subdomain, 256 / 512 threads; 3: persistent clusters,
+                             one pixel column per thread; the results do not depend
+                             on it                                                    */
 } dd_tv_batch_params;
 
 /* Validates and allocates the batch (images[n], n >= 1); *out = NULL on error. */

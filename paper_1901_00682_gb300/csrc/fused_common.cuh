@@ -190,6 +190,37 @@ struct PaLayout {
   static constexpr size_t BYTES = sizeof(float) * MB + 16;
 };
 
+// Source of the subdomains a persistent batch kernel iterates over: the number of
+// subdomains, their image's arguments and grid position, the strips that receive
+// their interface values, and a call of the tile body with the image's fidelity as a
+// compile-time constant (FidC).
+template <int V>
+struct FidC {
+  static constexpr int value = V;
+};
+
+// The batch's work list: (image, tile) with the fidelity, parameters and coefficients
+// of each image.
+struct BatchTiles {
+  const BatchArgs& B;
+  int total;
+  __device__ int count() const { return total; }
+  __device__ int inner() const { return B.args[0].K; }
+  __device__ int image(int t) const { return B.tile_img[t]; }
+  __device__ const LocalArgs& args(int t) const { return B.args[B.tile_img[t]]; }
+  __device__ int local(int t) const { return t - B.tile_base[B.tile_img[t]]; }
+  __device__ int fid(int t) const { return B.fid[B.tile_img[t]]; }
+  __device__ Strips out(int t) const { return B.strips[2 * B.tile_img[t] + B.write_set]; }
+  __device__ int* err() const { return B.args[0].err; }
+  template <class Body>
+  __device__ void dispatch(int t, Body&& body) const {
+    switch (fid(t)) {
+      case FID_L2: body(FidC<FID_L2>{}); break;
+      case FID_L1: body(FidC<FID_L1>{}); break;
+      default: body(FidC<FID_SEG>{}); break;
+    }
+  }
+};
 
 }  // namespace
 }  // namespace ddtv

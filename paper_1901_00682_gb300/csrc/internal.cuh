@@ -126,6 +126,8 @@ cudaError_t fused_pg_prepare();
 bool fused_mt_supported(const LocalArgs& a);
 cudaError_t launch_fused_mt(const LocalArgs& a, int fidelity, cudaStream_t st);
 cudaError_t fused_mt_prepare();
+// The same kernel over the work list of a batch (every image's arrays 16-byte aligned).
+cudaError_t launch_fused_mt_batch(const BatchArgs& B, int total_tiles, cudaStream_t st);
 
 // ---- kernels_fused_wrow.cu
 // Persistent fused local solver with one warp per pair of rows (named-barrier

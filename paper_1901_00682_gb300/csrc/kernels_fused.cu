@@ -1348,26 +1348,6 @@ __device__ __forceinline__ void fused_pa_body(const LocalArgs& A, const int firs
   if (timed_out) atomicOr(A.err, 1);
 }
 
-// The batch's work list as the source of the subdomains a persistent cluster iterates
-// over: (image, tile) with the fidelity, parameters and coefficients of each image.
-template <int V>
-struct FidC {
-  static constexpr int value = V;
-};
-
-struct BatchTiles {
-  const BatchArgs& B;
-  int total;
-  __device__ int count() const { return total; }
-  __device__ int inner() const { return B.args[0].K; }
-  __device__ int image(int t) const { return B.tile_img[t]; }
-  __device__ const LocalArgs& args(int t) const { return B.args[B.tile_img[t]]; }
-  __device__ int local(int t) const { return t - B.tile_base[B.tile_img[t]]; }
-  __device__ int fid(int t) const { return B.fid[B.tile_img[t]]; }
-  __device__ Strips out(int t) const { return B.strips[2 * B.tile_img[t] + B.write_set]; }
-  __device__ int* err() const { return B.args[0].err; }
-};
-
 // Persistent body over a source of subdomains of several images (the batch): the
 // single-image body above with, per subdomain, the image's geometry, parameters,
 // strips and fidelity (dispatched at run time), and the image's coefficients reloaded
@@ -2148,7 +2128,8 @@ cudaError_t fused_prepare() {
 cudaError_t launch_fused_batch(const BatchArgs& B, int total_tiles, int variant, cudaStream_t st) {
   if (variant == 1) return launch_async_batch<8, 2, 8, 2>(B, total_tiles, st);
   if (variant == 2) return launch_async_batch<8, 4, 4, 1>(B, total_tiles, st);
-  return launch_pa_batch<8, 2, 8, 2, true>(B, total_tiles, st);
+  if (variant == 3) return launch_pa_batch<8, 2, 8, 2, true>(B, total_tiles, st);
+  return launch_fused_mt_batch(B, total_tiles, st);
 }
 
 cudaError_t launch_fused_local(const LocalArgs& a, int fid, int variant, cudaStream_t st) {

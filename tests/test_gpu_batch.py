@@ -29,7 +29,7 @@ def _images():
     return out
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_batch_equals_single_image_solves_bitwise(variant):
     """Every batch mapping (0: persistent clusters over the work list; 1, 2: one
     cluster per subdomain) gives each image the bits of its own solve."""
