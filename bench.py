@@ -149,6 +149,15 @@ def load_jstar(f):
     return rec, None
 
 
+def kernel_source_sha():
+    """First 16 hex digits of the SHA-256 of the fused kernel's sources (the kernel file
+    and the device headers it includes), to tell whether a capture is still current."""
+    h = hashlib.sha256()
+    for name in ("kernels_fused_mt.cu", "fused_common.cuh", "pointwise.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1901_00682_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profile_traffic():
     """(dram bytes per launch, sha) of the fused kernel from the committed ncu summary,
     or None when the kernel source changed since the capture."""
@@ -159,9 +168,7 @@ def profile_traffic():
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    src = os.path.join(ROOT, "paper_1901_00682_gb300", "csrc", "kernels_fused.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if vals.get("kernel_source_sha256") != sha:
+    if vals.get("kernel_source_sha256") != kernel_source_sha():
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
