@@ -153,7 +153,7 @@ def kernel_source_sha():
     """First 16 hex digits of the SHA-256 of the fused kernel's sources (the kernel file
     and the device headers it includes), to tell whether a capture is still current."""
     h = hashlib.sha256()
-    for name in ("kernels_fused_mt.cu", "fused_common.cuh", "pointwise.cuh"):
+    for name in ("kernels_fused_mt4.cu", "fused_common.cuh", "pointwise.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1901_00682_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
@@ -346,7 +346,7 @@ def run_ours(args):
     roofline = {
         "bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s", "frac": achieved / smem_peak,
         "traffic": traffic,
-        "kernel": "fused local solver (k_fused_mt: persistent clusters of 8 CTAs x 256 threads, one 128x128 subdomain at a time, 2x4 pixel micro-tile per thread)",
+        "kernel": "fused local solver (k_fused_mt4: persistent clusters of 8 CTAs x 128 threads, 3 CTAs per SM, one 128x128 subdomain per cluster at a time, 4x4 pixel micro-tile per thread)",
         "peak_source": "measured live: ld.shared probe kernel (dd_tv_measure_smem_bandwidth)",
         "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": local_avg_ms,
         "hbm_state_stream": {"bytes_per_launch": 28 * H * W,

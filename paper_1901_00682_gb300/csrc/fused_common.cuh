@@ -162,6 +162,16 @@ __device__ __forceinline__ void st_async_v2(uint32_t remote_addr, float a, float
                : "memory");
 }
 
+// four floats into a neighbour CTA's shared memory (16-byte aligned), counted on its mbarrier
+__device__ __forceinline__ void st_async_v4_f32(uint32_t remote_addr, float a, float b, float c, float d,
+                                                uint32_t remote_mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+                   remote_addr),
+               "r"(__float_as_uint(a)), "r"(__float_as_uint(b)), "r"(__float_as_uint(c)), "r"(__float_as_uint(d)),
+               "r"(remote_mbar)
+               : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t addr, uint32_t bytes) {
   asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.release.cta.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(addr),
                "r"(bytes)

@@ -144,6 +144,14 @@ bool fused_ps_supported(const LocalArgs& a);
 cudaError_t launch_fused_ps(const LocalArgs& a, int fidelity, cudaStream_t st);
 cudaError_t fused_ps_prepare();
 
+// ---- kernels_fused_mt4.cu
+// Persistent fused local solver on 4 x 4 micro-tiles, one warp per thread row, three
+// 128-thread CTAs per SM; 128 x 128 tiles with 16-byte aligned rows
+// (fused_mt4_supported).
+bool fused_mt4_supported(const LocalArgs& a);
+cudaError_t launch_fused_mt4(const LocalArgs& a, int fidelity, cudaStream_t st);
+cudaError_t fused_mt4_prepare();
+
 // ---- kernels_plain.cu
 // phat = p~ -+ tau lambda on the interface sides, pbar = p~; full arrays.
 cudaError_t launch_plain_phat(const LocalArgs& a, float* Ph1, float* Ph2, float* Pb1, float* Pb2, cudaStream_t st);

@@ -1741,7 +1741,7 @@ constexpr Config kConfigs[] = {
     {128, 8, 4, 4, "bw128_r8_tr4_cl4"},    // class 2, variant 1: 512 threads, 1 CTA/SM
     {128, 16, 2, 4, "bw128_r16_tr2_cl4"},  // class 2, variant 2: 256 threads, 16 rows/thread
 };
-constexpr int kNumVariants = 14;
+constexpr int kNumVariants = 15;
 
 template <int BW, int R, int TR, int CL, int FID, bool MASK, bool ADAPT>
 cudaError_t launch_one(const LocalArgs& a, cudaStream_t st) {
@@ -2118,6 +2118,7 @@ cudaError_t fused_prepare() {
   if ((e = fused_mt_prepare()) != cudaSuccess) return e;
   if ((e = fused_wrow_prepare()) != cudaSuccess) return e;
   if ((e = fused_ps_prepare()) != cudaSuccess) return e;
+  if ((e = fused_mt4_prepare()) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_fused_async_batch<8, 2, 8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)AsyncLayout<8, 2>::BYTES)) != cudaSuccess)
     return e;
@@ -2138,7 +2139,8 @@ cudaError_t launch_fused_local(const LocalArgs& a, int fid, int variant, cudaStr
   if (a.inner_tol2 > 0.0) variant = 0;  // adaptive stopping: the cluster-barrier kernel only
   if (a.inner_tol2 <= 0.0 && a.g.H == 128 * a.g.NR && a.g.W == 128 * a.g.NC) {  // every tile exactly 128 x 128
     switch (variant) {
-      case 0:  // default: persistent, 2 x 4 micro-tiles, edge exchange only
+      case 0:  // default: persistent, 4 x 4 micro-tiles, one warp per thread row, 3 CTAs per SM
+        if (fused_mt4_supported(a)) return launch_fused_mt4(a, fid, st);
         return fused_mt_supported(a) ? launch_fused_mt(a, fid, st) : launch_pa<8, 2, 8, 2, true>(a, fid, st);
       case 1: return launch_async<8, 2, 8, 2>(a, fid, st);      // async halos, one subdomain per cluster
       case 2: return launch_full<8, 4, 4, 1>(a, fid, st);       // cluster barrier per half-step: 512 threads
@@ -2155,6 +2157,8 @@ cudaError_t launch_fused_local(const LocalArgs& a, int fid, int variant, cudaStr
         return fused_wrow_supported(a) ? launch_fused_wrow(a, fid, st) : launch_pa<8, 2, 8, 2, true>(a, fid, st);
       case 13:                                                  // variant 11 with 16-byte copies, out-buffer
         return fused_ps_supported(a) ? launch_fused_ps(a, fid, st) : launch_pa<8, 2, 8, 2, true>(a, fid, st);
+      case 14:                                                  // 2 x 4 micro-tiles, 256 threads, 2 CTAs per SM
+        return fused_mt_supported(a) ? launch_fused_mt(a, fid, st) : launch_pa<8, 2, 8, 2, true>(a, fid, st);
       default: return cudaErrorInvalidValue;
     }
   }

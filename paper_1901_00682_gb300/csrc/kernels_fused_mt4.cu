@@ -1,0 +1,507 @@
+// Persistent fused local solver on 4 x 4 micro-tiles, one warp per thread row
+// (128 x 128 subdomains).
+//
+// The 2 x 4 micro-tile kernel (kernels_fused_mt.cu) holds 8 pixels per thread in
+// 256-thread CTAs, two per SM.  Here a thread holds a micro-tile of four columns by
+// four rows (16 pixels), so per pixel half as many edge values cross between threads,
+// and a warp holds four full rows of the CTA's band: the exchange between horizontal
+// neighbours never leaves the warp.  A CTA is four warps (128 threads) covering a band
+// of 16 rows; with up to 170 registers per thread three CTAs fit on an SM, which then
+// interleaves three subdomain bands instead of two.  The tile's right side (the p2 dofs
+// of column 128) belongs to lane 31 (the holder of column 127), in registers; the
+// bottom side to the last warp of the last CTA.
+//
+// Per inner iteration a lane exchanges, with one 16-byte shared-memory access each, the
+// u of its right column (for the lane to its right), the pbar2 of its left edge (for
+// the lane to its left), and its warp's last-row u and first-row pbar1 with the warps
+// above and below; two CTA barriers order them.  Rows crossing CTAs travel with
+// st.async and mbarrier complete_tx (bounded waits, the same phase protocol as
+// fused_pa_body), and the next subdomain is prefetched with 16-byte cp.async copies
+// (p2 as a window starting on a 16-byte boundary: W + N_c must be a multiple of 4).
+// Rows are packed in pairs (r, r + 2) for the `*.f32x2` arithmetic; every value is
+// computed with the operations of the scalar iteration in the same order, so the
+// results are bit-identical to the other mappings.
+#include "fused_common.cuh"
+#include "internal.cuh"
+
+namespace ddtv {
+
+namespace {
+
+struct Mt4Layout {
+  static constexpr int CL = 8, NW = 4, BAND = 4 * NW, BW = 128, NT = 32 * NW;
+  static constexpr int P2S = 132;                    // staged p2 row: 132 floats from a 16-byte boundary
+  static constexpr int SLOT = 4 * 33;                // one warp's UR / QL slots
+  // (NW + 1) x 128, column order: row 0 = u of the row above the band (halo; zero in
+  // the first CTA), row w + 1 = u of warp w's last row
+  static constexpr int UB = 0;
+  // (NW + 1) x 128, column order: row w = pbar1 of warp w's first row, row NW = pbar1
+  // of the row below the band (halo, or the tile's bottom side)
+  static constexpr int Q1 = UB + (NW + 1) * BW;
+  // NW x 33 x 4, pair order: slot 0 = zero (left of the tile), slot l + 1 = u of lane
+  // l's right column
+  static constexpr int UR = Q1 + (NW + 1) * BW;
+  static constexpr int QL = UR + NW * SLOT;          // NW x 33 x 4: slot l = pbar2 of lane l's left edge
+  static constexpr int F = QL + NW * SLOT;           // NW x 4 (column) x 32 (lane) x 4: f (or g), pair order
+  static constexpr int CO = F + NW * 4 * 32 * 4;     // kMaxSmemCoef x 8 coefficients
+  static constexpr int kMaxSmemCoef = 64;
+  static constexpr int SU = CO + 8 * kMaxSmemCoef;   // staging of the next subdomain: u, f, p1 (BAND x 128 each)
+  static constexpr int SP2 = SU + 3 * BAND * BW;     // p2 window (BAND x P2S)
+  static constexpr int XLT = SP2 + BAND * P2S;       // lamh above the tile (128)
+  static constexpr int XPB = XLT + BW;               // p1 of the tile's bottom side (128)
+  static constexpr int XLB = XPB + BW;               // lamh below the tile (128)
+  static constexpr int XQH = XLB + BW;               // p1 of the first row below the band (128)
+  static constexpr int XLL = XQH + BW;               // lamv left of the band rows (BAND)
+  static constexpr int XLR = XLL + BAND;             // lamv right of the band rows (BAND)
+  static constexpr int PBS = XLR + BAND;             // bottom side p of the tile (128; last CTA)
+  static constexpr int HBS = PBS + BW;               // bottom side phat (128)
+  static constexpr int HRS = HBS + BW;               // right side phat per warp (NW x 4, pair order)
+  static constexpr int MB = HRS + 4 * NW;            // two mbarriers
+  static constexpr size_t BYTES = sizeof(float) * MB + 16;
+  static_assert(Q1 % 4 == 0 && UR % 4 == 0 && QL % 4 == 0 && F % 4 == 0 && CO % 4 == 0 && SU % 4 == 0 &&
+                    SP2 % 4 == 0 && XLT % 4 == 0 && XLL % 4 == 0 && XLR % 4 == 0 && PBS % 4 == 0 &&
+                    HBS % 4 == 0 && HRS % 4 == 0 && MB % 2 == 0,
+                "16-byte alignment of the vector and cp.async buffers");
+  static_assert(CL * BAND == 128, "a cluster of CTAs covers the 128 rows of a tile");
+};
+
+__device__ __forceinline__ float lane4(f32x2 v, int h) { return h ? hi2(v) : lo2(v); }
+
+template <int FID, bool MASK>
+__device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const int first, const int stride) {
+  using L = Mt4Layout;
+  constexpr int NW = L::NW, CL = L::CL, BAND = L::BAND, NT = L::NT, BW = L::BW;
+  extern __shared__ __align__(16) float smem[];
+  float* sUB = smem + L::UB;
+  float* sQ1 = smem + L::Q1;
+  float* sCo = smem + L::CO;
+  const uint32_t mbU = smem_addr(smem + L::MB);
+  const uint32_t mbQ = mbU + 8;
+
+  const Grid g = A.g;
+  const int T = g.NR * g.NC;
+  const int rank = (int)blockIdx.x;
+  const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+  const int j0 = 4 * l;              // the lane's first column in the tile
+  const int lr0 = 4 * w;             // the warp's first row in the band
+  const int i0 = rank * BAND + lr0;  // ... in the tile
+  const int W2 = g.W + g.NC;
+  const float tau = A.tau;
+  const int K = A.K;
+  const bool last_row_here = rank == CL - 1 && w == NW - 1;
+  const bool push_down = w == NW - 1 && rank + 1 < CL;  // sends u of the band's last row
+  const bool push_up = w == 0 && rank > 0;              // sends pbar1 of the band's first row
+  const bool need_uh = push_up;
+  const bool need_qh = push_down;
+  constexpr uint32_t kHaloBytes = 4 * BW;
+  float* const myUR = smem + L::UR + w * L::SLOT + 4 * (l + 1);
+  float* const myQL = smem + L::QL + w * L::SLOT + 4 * l;
+  float* const myF = smem + L::F + (w * 4 * 32 + l) * 4;  // column c at + c * 128
+  uint32_t remote_u = 0, remote_q1 = 0, remote_mbU = 0, remote_mbQ = 0;
+  if (push_down) {
+    remote_u = map_rank(smem_addr(sUB + j0), rank + 1);
+    remote_mbU = map_rank(mbU, rank + 1);
+  }
+  if (push_up) {
+    remote_q1 = map_rank(smem_addr(sQ1 + NW * BW + j0), rank - 1);
+    remote_mbQ = map_rank(mbQ, rank - 1);
+  }
+  if (tid == 0) {
+    mbar_init(mbU, 1);
+    mbar_init(mbQ, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int q = tid; q < 8 * min(K, L::kMaxSmemCoef); q += NT) sCo[q] = reinterpret_cast<const float*>(A.coef)[q];
+  if (rank == 0 && w == 0) *reinterpret_cast<float4*>(sUB + j0) = make_float4(0.f, 0.f, 0.f, 0.f);  // u above the tile
+  if (l < 4) smem[L::UR + w * L::SLOT + l] = 0.f;  // u left of the tile
+  __syncthreads();
+  if (need_uh && l == 0) mbar_arrive_expect_tx(mbU, kHaloBytes);
+  if (need_qh && l == 0) mbar_arrive_expect_tx(mbQ, kHaloBytes);
+  cluster_arrive<true>();  // barriers initialised and armed everywhere before any halo is sent
+  cluster_wait();
+
+  auto prefetch = [&](int t) {
+    const int a = t / g.NC, b = t - a * g.NC;
+    const int c0 = b * 128;
+    const int gb = a * 128 + rank * BAND;  // image row of the band's first row
+#pragma unroll
+    for (int m = 0; m < 12; ++m) {  // u, f, p1: 3 x BAND rows x 32 chunks of 16 bytes
+      const int fld = m >> 2;
+      const int q = tid + NT * (m & 3);
+      const int row = q >> 5, ch = q & 31;
+      const float* base = fld == 0 ? A.u : (fld == 1 ? A.f : A.P1);
+      const int grow = gb + row + (fld == 2 ? a : 0);
+      cp_async16(smem + L::SU + fld * BAND * BW + row * BW + 4 * ch, base + (size_t)grow * g.W + c0 + 4 * ch);
+    }
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {  // p2 window: BAND rows x 33 chunks
+      const int q = tid + NT * m;
+      if (q < BAND * 33) {
+        const int row = q / 33, ch = q - row * 33;
+        cp_async16(smem + L::SP2 + row * L::P2S + 4 * ch, A.P2 + (size_t)(gb + row) * W2 + c0 + b - (b & 3) + 4 * ch);
+      }
+    }
+    if (tid < 32) {
+      if (rank == 0 && a > 0) cp_async16(smem + L::XLT + 4 * tid, A.lamh + (size_t)(a - 1) * g.W + c0 + 4 * tid);
+      if (tid < 4 && b > 0) cp_async16(smem + L::XLL + 4 * tid, A.lamv + (size_t)(b - 1) * g.H + gb + 4 * tid);
+    } else if (tid < 64) {
+      const int q = tid - 32;
+      if (rank == CL - 1 && a + 1 < g.NR)
+        cp_async16(smem + L::XPB + 4 * q, A.P1 + (size_t)(a * 128 + 128 + a) * g.W + c0 + 4 * q);
+      if (q < 4 && b + 1 < g.NC) cp_async16(smem + L::XLR + 4 * q, A.lamv + (size_t)b * g.H + gb + 4 * q);
+    } else if (tid < 96) {
+      const int q = tid - 64;
+      if (rank == CL - 1 && a + 1 < g.NR) cp_async16(smem + L::XLB + 4 * q, A.lamh + (size_t)a * g.W + c0 + 4 * q);
+    } else {
+      const int q = tid - 96;
+      if (rank < CL - 1) cp_async16(smem + L::XQH + 4 * q, A.P1 + (size_t)(gb + BAND + a) * g.W + c0 + 4 * q);
+    }
+    cp_async_commit();
+  };
+
+  bool timed_out = false;
+  uint32_t phU = 0, phQ = 0;  // index of the next phase of mbU / mbQ this CTA waits for
+  auto wait_u = [&]() {
+    if (!mbar_wait(mbU, phU & 1)) timed_out = true;
+    ++phU;
+    if (l == 0) mbar_arrive_expect_tx(mbU, kHaloBytes);  // arm the next phase
+  };
+  auto wait_q = [&]() {
+    if (!mbar_wait(mbQ, phQ & 1)) timed_out = true;
+    ++phQ;
+    if (l == 0) mbar_arrive_expect_tx(mbQ, kHaloBytes);
+  };
+
+  if (first < T) prefetch(first);
+
+  for (int t = first; t < T; t += stride) {
+    const int a = t / g.NC, b = t - a * g.NC;
+    const int c0 = b * 128;
+    const int gb = a * 128 + rank * BAND;
+    const int o = b & 3;
+    const bool s_top = a > 0, s_bot = a + 1 < g.NR, s_lft = b > 0, s_rgt = b + 1 < g.NC;
+    const float lim_left = (l == 0 && !s_lft) ? 0.f : 1.f;
+    const float lim_top = (i0 == 0 && !s_top) ? 0.f : 1.f;
+    const bool right_owner = s_rgt && l == 31;
+    // pairs [column c][e]: rows (e, e + 2) of column j0 + c
+    f32x2 U[4][2], P1[4][2], P2[4][2], H1[4][2], H2[4][2], Q1[4][2], Q2[4][2];
+    f32x2 PR[2] = {0ull, 0ull}, QR[2] = {0ull, 0ull};  // right side p, pbar (lane 31; phat in shared memory)
+    uint32_t in_d = 0;  // bit 4c + r: pixel (row r, column j0 + c) lies in the inpainting domain
+
+    cp_async_wait_all();
+    __syncthreads();  // staging landed; the previous subdomain's shared arrays are free
+    {
+      f32x2 FV[4][2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {  // rows e and e + 2 form the pairs of index e
+        float u[2][4], fv[2][4], p1[2][4], p2[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r = e + 2 * h, br = lr0 + r;
+          const float4 uu = *reinterpret_cast<const float4*>(smem + L::SU + br * BW + j0);
+          const float4 ff = *reinterpret_cast<const float4*>(smem + L::SU + BAND * BW + br * BW + j0);
+          const float4 pp = *reinterpret_cast<const float4*>(smem + L::SU + 2 * BAND * BW + br * BW + j0);
+          const float* p2s = smem + L::SP2 + br * L::P2S + o + j0;
+          u[h][0] = uu.x;
+          u[h][1] = uu.y;
+          u[h][2] = uu.z;
+          u[h][3] = uu.w;
+          fv[h][0] = ff.x;
+          fv[h][1] = ff.y;
+          fv[h][2] = ff.z;
+          fv[h][3] = ff.w;
+          p1[h][0] = pp.x;
+          p1[h][1] = pp.y;
+          p1[h][2] = pp.z;
+          p1[h][3] = pp.w;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            p2[h][c] = p2s[c];
+            if (FID == FID_SEG) fv[h][c] = (fv[h][c] - A.c1) * (fv[h][c] - A.c1) - (fv[h][c] - A.c2) * (fv[h][c] - A.c2);
+            if (MASK && A.mask[(size_t)(gb + br) * g.W + c0 + j0 + c]) in_d |= 1u << (4 * c + r);
+          }
+        }
+        if (e == 0) {
+          // the first row's pbar1, read by the warp above in its u-step 0
+          *reinterpret_cast<float4*>(sQ1 + w * BW + j0) = make_float4(p1[0][0], p1[0][1], p1[0][2], p1[0][3]);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float h1[2] = {p1[0][c], p1[1][c]}, h2[2] = {p2[0][c], p2[1][c]};
+          if (e == 0 && i0 == 0 && s_top) h1[0] = phat_t(p1[0][c], smem[L::XLT + j0 + c], tau);
+          if (c == 0 && l == 0 && s_lft) {
+            h2[0] = phat_t(p2[0][0], smem[L::XLL + lr0 + e], tau);
+            h2[1] = phat_t(p2[1][0], smem[L::XLL + lr0 + e + 2], tau);
+          }
+          U[c][e] = pk2(u[0][c], u[1][c]);
+          P1[c][e] = pk2(p1[0][c], p1[1][c]);
+          P2[c][e] = pk2(p2[0][c], p2[1][c]);
+          H1[c][e] = pk2(h1[0], h1[1]);
+          H2[c][e] = pk2(h2[0], h2[1]);
+          Q1[c][e] = P1[c][e];
+          Q2[c][e] = P2[c][e];
+          FV[c][e] = pk2(fv[0][c], fv[1][c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) *reinterpret_cast<ulonglong2*>(myF + c * 128) = make_ulonglong2(FV[c][0], FV[c][1]);
+      *reinterpret_cast<ulonglong2*>(myQL) = make_ulonglong2(P2[0][0], P2[0][1]);
+      if (last_row_here) {
+        float pB[4] = {0.f, 0.f, 0.f, 0.f}, hB[4] = {0.f, 0.f, 0.f, 0.f};
+        if (s_bot) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            pB[c] = smem[L::XPB + j0 + c];
+            hB[c] = phat_s(pB[c], smem[L::XLB + j0 + c], tau);
+          }
+        }
+        const float4 pv = make_float4(pB[0], pB[1], pB[2], pB[3]);
+        *reinterpret_cast<float4*>(smem + L::PBS + j0) = pv;
+        *reinterpret_cast<float4*>(smem + L::HBS + j0) = make_float4(hB[0], hB[1], hB[2], hB[3]);
+        *reinterpret_cast<float4*>(sQ1 + NW * BW + j0) = pv;
+      }
+      if (need_qh)
+        *reinterpret_cast<float4*>(sQ1 + NW * BW + j0) = *reinterpret_cast<const float4*>(smem + L::XQH + j0);
+      if (right_owner) {
+        float pr[4], hr[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          pr[r] = smem[L::SP2 + (lr0 + r) * L::P2S + o + 128];
+          hr[r] = phat_s(pr[r], smem[L::XLR + lr0 + r], tau);
+        }
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          PR[e] = pk2(pr[e], pr[e + 2]);
+          QR[e] = PR[e];
+        }
+        *reinterpret_cast<ulonglong2*>(smem + L::HRS + 4 * w) = make_ulonglong2(pk2(hr[0], hr[2]), pk2(hr[1], hr[3]));
+      }
+    }
+    __syncthreads();  // staging consumed by every thread
+    if (t + stride < T) prefetch(t + stride);
+
+    for (int k = 0; k < K; ++k) {
+      Coef co;
+      if (k < L::kMaxSmemCoef) {
+        const float4 ca = *reinterpret_cast<const float4*>(sCo + 8 * k);
+        const float4 cb = *reinterpret_cast<const float4*>(sCo + 8 * k + 4);
+        co = Coef{ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+      } else {
+        co = A.coef[k];
+      }
+      const f32x2 SIG = pk2(co.sig, co.sig), UA = pk2(co.ua, co.ua), UB = pk2(co.ub, co.ub);
+      const f32x2 PA = pk2(co.pa, co.pa), PC = pk2(co.pc, co.pc), PB = pk2(co.pb, co.pb), TH = pk2(co.th, co.th);
+      if (need_qh && k > 0) wait_q();  // pbar1 halo of iteration k-1
+      // ---- u-step: pair e = 1 (holding the warp's last row) first
+      {
+        const float4 qb = *reinterpret_cast<const float4*>(sQ1 + (w + 1) * BW + j0);  // pbar1 of the row below
+        const ulonglong2 qn = *reinterpret_cast<const ulonglong2*>(myQL + 4);         // left edge of the lane to the right
+        const f32x2 QRn[2] = {l == 31 ? QR[0] : qn.x, l == 31 ? QR[1] : qn.y};
+        const float qbv[4] = {qb.x, qb.y, qb.z, qb.w};
+#pragma unroll
+        for (int ee = 0; ee < 2; ++ee) {
+          const int e = 1 - ee;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const ulonglong2 fc = *reinterpret_cast<const ulonglong2*>(myF + c * 128);
+            const f32x2 fg = e == 0 ? fc.x : fc.y;
+            const f32x2 below = e == 0 ? Q1[c][1] : pk2(hi2(Q1[c][0]), qbv[c]);
+            const f32x2 right = c < 3 ? Q2[c + 1][e] : QRn[e];
+            const f32x2 d = sub2(add2(sub2(below, Q1[c][e]), right), Q2[c][e]);  // div_px
+            const f32x2 ub = fma2(SIG, d, U[c][e]);
+            const bool dl = MASK && ((in_d >> (4 * c + e)) & 1u), dh = MASK && ((in_d >> (4 * c + e + 2)) & 1u);
+            f32x2 un;
+            if (FID == FID_L2) {
+              un = fma2(UB, fg, mul2(UA, ub));
+              if (MASK) un = pk2(dl ? lo2(ub) : lo2(un), dh ? hi2(ub) : hi2(un));
+            } else {
+              un = pk2(prox_ubar<FID>(lo2(ub), lo2(fg), dl, co), prox_ubar<FID>(hi2(ub), hi2(fg), dh, co));
+            }
+            U[c][e] = un;
+          }
+          if (e == 1 && push_down)
+            st_async_v4_f32(remote_u, hi2(U[0][1]), hi2(U[1][1]), hi2(U[2][1]), hi2(U[3][1]), remote_mbU);
+        }
+        *reinterpret_cast<ulonglong2*>(myUR) = make_ulonglong2(U[3][0], U[3][1]);
+        if (w < NW - 1)
+          *reinterpret_cast<float4*>(sUB + (w + 1) * BW + j0) =
+              make_float4(hi2(U[0][1]), hi2(U[1][1]), hi2(U[2][1]), hi2(U[3][1]));
+      }
+      __syncthreads();
+      if (need_uh) wait_u();  // u halo of iteration k
+      // ---- p-step: pair e = 0 (holding the warp's first row) first
+      {
+        const float4 ua = *reinterpret_cast<const float4*>(sUB + w * BW + j0);  // u of the row above
+        const ulonglong2 ul = *reinterpret_cast<const ulonglong2*>(myUR - 4);  // right column of the lane to the left
+        const float uav[4] = {ua.x, ua.y, ua.z, ua.w};
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const f32x2 above = e == 1 ? U[c][0] : pk2(uav[c], lo2(U[c][1]));
+            const f32x2 leftu = c > 0 ? U[c - 1][e] : (e == 0 ? ul.x : ul.y);
+            {
+              const f32x2 tt = fma2(PC, sub2(U[c][e], above), fma2(PA, P1[c][e], mul2(PB, H1[c][e])));  // p_target
+              const float l0 = e == 0 ? lim_top : 1.f;
+              const f32x2 pn = pk2(fminf(fmaxf(lo2(tt), -l0), l0), fminf(fmaxf(hi2(tt), -1.f), 1.f));
+              Q1[c][e] = fma2(TH, sub2(pn, P1[c][e]), pn);
+              P1[c][e] = pn;
+            }
+            {
+              const f32x2 tt = fma2(PC, sub2(U[c][e], leftu), fma2(PA, P2[c][e], mul2(PB, H2[c][e])));
+              const float ll = c == 0 ? lim_left : 1.f;
+              const f32x2 pn = pk2(fminf(fmaxf(lo2(tt), -ll), ll), fminf(fmaxf(hi2(tt), -ll), ll));
+              Q2[c][e] = fma2(TH, sub2(pn, P2[c][e]), pn);
+              P2[c][e] = pn;
+            }
+          }
+          if (e == 0) {
+            const float4 q = make_float4(lo2(Q1[0][0]), lo2(Q1[1][0]), lo2(Q1[2][0]), lo2(Q1[3][0]));
+            if (w > 0) *reinterpret_cast<float4*>(sQ1 + w * BW + j0) = q;
+            if (push_up) st_async_v4_f32(remote_q1, q.x, q.y, q.z, q.w, remote_mbQ);
+          }
+        }
+        *reinterpret_cast<ulonglong2*>(myQL) = make_ulonglong2(Q2[0][0], Q2[0][1]);
+      }
+      if (right_owner) {  // the right side's dofs, Du = -u of column 127 (pc (-u) = (-pc) u exactly)
+        const f32x2 NPC = pk2(-co.pc, -co.pc);
+        const ulonglong2 hrv = *reinterpret_cast<const ulonglong2*>(smem + L::HRS + 4 * w);
+        const f32x2 HR[2] = {hrv.x, hrv.y};
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const f32x2 tt = fma2(NPC, U[3][e], fma2(PA, PR[e], mul2(PB, HR[e])));
+          const f32x2 pn = pk2(fminf(fmaxf(lo2(tt), -1.f), 1.f), fminf(fmaxf(hi2(tt), -1.f), 1.f));
+          QR[e] = fma2(TH, sub2(pn, PR[e]), pn);
+          PR[e] = pn;
+        }
+      }
+      if (last_row_here && s_bot) {
+        const float4 pv = *reinterpret_cast<const float4*>(smem + L::PBS + j0);
+        const float4 hv = *reinterpret_cast<const float4*>(smem + L::HBS + j0);
+        float pB[4] = {pv.x, pv.y, pv.z, pv.w}, qB[4];
+        const float hB[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) p_update(pB[c], qB[c], -hi2(U[c][1]), hB[c], co);
+        *reinterpret_cast<float4*>(smem + L::PBS + j0) = make_float4(pB[0], pB[1], pB[2], pB[3]);
+        *reinterpret_cast<float4*>(sQ1 + NW * BW + j0) = make_float4(qB[0], qB[1], qB[2], qB[3]);
+      }
+      __syncthreads();
+    }
+    if (need_qh) wait_q();  // drain the last pbar1 halo (not read)
+
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int e = r & 1, h = r >> 1;
+      const int gi = gb + lr0 + r;
+      *reinterpret_cast<float4*>(A.u + (size_t)gi * g.W + c0 + j0) =
+          make_float4(lane4(U[0][e], h), lane4(U[1][e], h), lane4(U[2][e], h), lane4(U[3][e], h));
+      *reinterpret_cast<float4*>(A.P1 + (size_t)(gi + a) * g.W + c0 + j0) =
+          make_float4(lane4(P1[0][e], h), lane4(P1[1][e], h), lane4(P1[2][e], h), lane4(P1[3][e], h));
+      float* p2row = A.P2 + (size_t)gi * W2 + c0 + b + j0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) p2row[c] = lane4(P2[c][e], h);
+      if (l == 0 && s_lft) A.out.SL[(size_t)(b - 1) * g.H + gi] = lane4(P2[0][e], h);
+      if (right_owner) {
+        const float pr = lane4(PR[e], h);
+        A.P2[(size_t)gi * W2 + c0 + 128 + b] = pr;
+        A.out.SR[(size_t)b * g.H + gi] = pr;
+      }
+    }
+    if (i0 == 0 && s_top)
+      *reinterpret_cast<float4*>(A.out.ST + (size_t)(a - 1) * g.W + c0 + j0) =
+          make_float4(lo2(P1[0][0]), lo2(P1[1][0]), lo2(P1[2][0]), lo2(P1[3][0]));
+    if (last_row_here && s_bot) {
+      const float4 v = *reinterpret_cast<const float4*>(smem + L::PBS + j0);
+      *reinterpret_cast<float4*>(A.P1 + (size_t)(a * 128 + 128 + a) * g.W + c0 + j0) = v;
+      *reinterpret_cast<float4*>(A.out.SB + (size_t)a * g.W + c0 + j0) = v;
+    }
+  }
+  cp_async_wait_all();
+  cluster_arrive<true>();  // no CTA leaves while a neighbour may still write into it
+  cluster_wait();
+  if (timed_out) atomicOr(A.err, 1);
+}
+
+template <int FID, bool MASK>
+__global__ void __launch_bounds__(Mt4Layout::NT, 3) k_fused_mt4(const LocalArgs A) {
+  fused_mt4_body<FID, MASK>(A, blockIdx.y, gridDim.y);
+}
+
+template <int FID, bool MASK>
+int& mt4_clusters(int dev) {
+  static int n[64] = {0};
+  return n[dev & 63];
+}
+
+cudaLaunchConfig_t mt4_config(int clusters, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(Mt4Layout::CL, clusters, 1);
+  cfg.blockDim = dim3(Mt4Layout::NT, 1, 1);
+  cfg.dynamicSmemBytes = Mt4Layout::BYTES;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = Mt4Layout::CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+template <int FID, bool MASK>
+cudaError_t prepare_mt4_one() {
+  auto kern = k_fused_mt4<FID, MASK>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Mt4Layout::BYTES);
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = mt4_config(1024, attr);
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  mt4_clusters<FID, MASK>(dev) = n;
+  return cudaSuccess;
+}
+
+template <int FID, bool MASK>
+cudaError_t launch_mt4_one(const LocalArgs& a, cudaStream_t st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int tiles = a.g.NR * a.g.NC;
+  int nc = mt4_clusters<FID, MASK>(dev);
+  if (nc <= 0 || nc > tiles) nc = tiles;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = mt4_config(nc, attr);
+  cfg.stream = st;
+  return cudaLaunchKernelEx(&cfg, k_fused_mt4<FID, MASK>, a);
+}
+
+}  // namespace
+
+bool fused_mt4_supported(const LocalArgs& a) {
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  return a.g.H == 128 * a.g.NR && a.g.W == 128 * a.g.NC && (a.g.W + a.g.NC) % 4 == 0 && al16(a.u) && al16(a.f) &&
+         al16(a.P1) && al16(a.P2) && al16(a.lamh) && al16(a.lamv) && al16(a.out.ST) && al16(a.out.SB);
+}
+
+cudaError_t fused_mt4_prepare() {
+  cudaError_t e;
+  if ((e = prepare_mt4_one<FID_L2, false>()) != cudaSuccess) return e;
+  if ((e = prepare_mt4_one<FID_L2, true>()) != cudaSuccess) return e;
+  if ((e = prepare_mt4_one<FID_L1, false>()) != cudaSuccess) return e;
+  if ((e = prepare_mt4_one<FID_L1, true>()) != cudaSuccess) return e;
+  return prepare_mt4_one<FID_SEG, false>();
+}
+
+cudaError_t launch_fused_mt4(const LocalArgs& a, int fid, cudaStream_t st) {
+  const bool m = a.mask != nullptr;
+  switch (fid) {
+    case FID_L2: return m ? launch_mt4_one<FID_L2, true>(a, st) : launch_mt4_one<FID_L2, false>(a, st);
+    case FID_L1: return m ? launch_mt4_one<FID_L1, true>(a, st) : launch_mt4_one<FID_L1, false>(a, st);
+    default: return launch_mt4_one<FID_SEG, false>(a, st);
+  }
+}
+
+}  // namespace ddtv
