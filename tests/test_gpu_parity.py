@@ -234,17 +234,17 @@ def test_variant_count():
 @pytest.mark.parametrize("fid,mask_prob,K", [("l2", 0.2, 10), ("l1", 0.2, 10), ("seg", 0.0, 10), ("l2", 0.0, 70)])
 def test_persistent_variants_bitwise_all_fidelities(fid, mask_prob, K):
     """The default 4 x 4 micro-tile mapping against the column (11), warp-row (12),
-    16-byte-copy (13) and 2 x 4 micro-tile (14) mappings for every fidelity, with and without the inpainting mask,
-    and with more inner iterations than the kernels keep in shared memory (K = 70:
-    coefficients 64.. come from global memory)."""
+    16-byte-copy (13) and 2 x 4 micro-tile (14) mappings for every fidelity, with and
+    without the inpainting mask, and with more inner iterations than the kernels keep
+    in shared memory (K = 70: coefficients 64.. come from global memory)."""
     L = _gpu()
-    H, W = 384, 256
+    H, W = 384, 512  # 3 x 4 tiles: W + N_c = 516 keeps the p2 rows 16-byte aligned (variants 0, 12, 13)
     f, _ = synth.rof_image(H, W, 12, 0.1, 5)
     mask = None
     if mask_prob:
         mask = synth.bernoulli_mask((H, W), mask_prob, np.random.Generator(np.random.PCG64(9)))
         f = np.where(mask == 1, 0.0, f).astype(np.float32)
-    kw = dict(sub_rows=3, sub_cols=2, fidelity=fid, alpha={"l2": 8.0, "l1": 1.5, "seg": 20.0}[fid],
+    kw = dict(sub_rows=3, sub_cols=4, fidelity=fid, alpha={"l2": 8.0, "l1": 1.5, "seg": 20.0}[fid],
               inner_iters=K)
     if fid == "seg":
         kw.update(c1=0.2, c2=0.8, tau=1.0)
@@ -254,9 +254,12 @@ def test_persistent_variants_bitwise_all_fidelities(fid, mask_prob, K):
             assert np.array_equal(outs[0][k], o[k]), k
 
 
-@pytest.mark.parametrize("H,W,NR,NC", [(384, 384, 3, 3), (250, 260, 2, 3), (128, 128, 1, 1), (1024, 1280, 8, 10)])
+@pytest.mark.parametrize("H,W,NR,NC", [(384, 384, 3, 3), (250, 260, 2, 3), (128, 128, 1, 1), (1024, 1280, 8, 10),
+                                        (512, 512, 4, 4), (1024, 1024, 8, 8)])
 def test_fused_variants_bitwise_identical(H, W, NR, NC):
-    """Every hardware mapping of a 128x128-class subdomain runs the same arithmetic."""
+    """Every hardware mapping of a 128x128-class subdomain runs the same arithmetic.
+    W + N_c a multiple of 4 (512 / 4 x 4, 1024 / 8 x 8) runs the mappings that copy p2
+    rows in 16-byte chunks; the other grids run their fallback (variant 11 or 14)."""
     L = _gpu()
     f, _ = synth.rof_image(H, W, 12, 0.1, 12)
     outs = []
