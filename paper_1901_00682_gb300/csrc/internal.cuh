@@ -149,7 +149,9 @@ cudaError_t fused_ps_prepare();
 // 128-thread CTAs per SM; 128 x 128 tiles with 16-byte aligned rows
 // (fused_mt4_supported).
 bool fused_mt4_supported(const LocalArgs& a);
-cudaError_t launch_fused_mt4(const LocalArgs& a, int fidelity, cudaStream_t st);
+// tma: move the state with tensor copies (falls back to cp.async if the tensor maps
+// cannot be encoded)
+cudaError_t launch_fused_mt4(const LocalArgs& a, int fidelity, bool tma, cudaStream_t st);
 cudaError_t fused_mt4_prepare();
 
 // ---- kernels_plain.cu

@@ -1741,7 +1741,7 @@ constexpr Config kConfigs[] = {
     {128, 8, 4, 4, "bw128_r8_tr4_cl4"},    // class 2, variant 1: 512 threads, 1 CTA/SM
     {128, 16, 2, 4, "bw128_r16_tr2_cl4"},  // class 2, variant 2: 256 threads, 16 rows/thread
 };
-constexpr int kNumVariants = 15;
+constexpr int kNumVariants = 16;
 
 template <int BW, int R, int TR, int CL, int FID, bool MASK, bool ADAPT>
 cudaError_t launch_one(const LocalArgs& a, cudaStream_t st) {
@@ -2139,8 +2139,8 @@ cudaError_t launch_fused_local(const LocalArgs& a, int fid, int variant, cudaStr
   if (a.inner_tol2 > 0.0) variant = 0;  // adaptive stopping: the cluster-barrier kernel only
   if (a.inner_tol2 <= 0.0 && a.g.H == 128 * a.g.NR && a.g.W == 128 * a.g.NC) {  // every tile exactly 128 x 128
     switch (variant) {
-      case 0:  // default: persistent, 4 x 4 micro-tiles, one warp per thread row, 3 CTAs per SM
-        if (fused_mt4_supported(a)) return launch_fused_mt4(a, fid, st);
+      case 0:  // default: persistent, 4 x 4 micro-tiles, one warp per thread row, 3 CTAs per SM, tensor copies
+        if (fused_mt4_supported(a)) return launch_fused_mt4(a, fid, true, st);
         return fused_mt_supported(a) ? launch_fused_mt(a, fid, st) : launch_pa<8, 2, 8, 2, true>(a, fid, st);
       case 1: return launch_async<8, 2, 8, 2>(a, fid, st);      // async halos, one subdomain per cluster
       case 2: return launch_full<8, 4, 4, 1>(a, fid, st);       // cluster barrier per half-step: 512 threads
@@ -2159,6 +2159,8 @@ cudaError_t launch_fused_local(const LocalArgs& a, int fid, int variant, cudaStr
         return fused_ps_supported(a) ? launch_fused_ps(a, fid, st) : launch_pa<8, 2, 8, 2, true>(a, fid, st);
       case 14:                                                  // 2 x 4 micro-tiles, 256 threads, 2 CTAs per SM
         return fused_mt_supported(a) ? launch_fused_mt(a, fid, st) : launch_pa<8, 2, 8, 2, true>(a, fid, st);
+      case 15:                                                  // variant 0 moving the state with cp.async
+        return fused_mt4_supported(a) ? launch_fused_mt4(a, fid, false, st) : launch_pa<8, 2, 8, 2, true>(a, fid, st);
       default: return cudaErrorInvalidValue;
     }
   }

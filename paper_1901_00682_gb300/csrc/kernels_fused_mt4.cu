@@ -21,6 +21,16 @@
 // Rows are packed in pairs (r, r + 2) for the `*.f32x2` arithmetic; every value is
 // computed with the operations of the scalar iteration in the same order, so the
 // results are bit-identical to the other mappings.
+//
+// TMA: the same kernel moving the state with the tensor memory accelerator.  One thread
+// loads the next subdomain's u, f, p1 bands and p2 window as four 2-D tensor copies
+// (cp.async.bulk.tensor, completion counted on an mbarrier), and stores the previous
+// subdomain's u and p1 bands from an out-buffer in shared memory as two tensor copies
+// (bulk group, issued after the barrier that follows the out-buffer writes; the buffer
+// is rewritten only after a wait for the copies to have read it); p2 and the sides go
+// out with ordinary stores.
+#include <cuda.h>
+
 #include "fused_common.cuh"
 #include "internal.cuh"
 
@@ -58,25 +68,58 @@ struct Mt4Layout {
   static constexpr int HRS = HBS + BW;               // right side phat per warp (NW x 4, pair order)
   static constexpr int MB = HRS + 4 * NW;            // two mbarriers
   static constexpr size_t BYTES = sizeof(float) * MB + 16;
+  // tensor-copy variant: out-buffers of u and p1 (128-byte aligned), three mbarriers
+  static constexpr int OU = (HRS + 4 * NW + 31) & ~31;
+  static constexpr int OP1 = OU + BAND * BW;
+  static constexpr int MBT = OP1 + BAND * BW;
+  static constexpr size_t BYTES_TMA = sizeof(float) * MBT + 32;
+  static constexpr uint32_t kTmaBytes = 4 * (3 * BAND * BW + BAND * P2S);  // one subdomain's four tensor loads
   static_assert(Q1 % 4 == 0 && UR % 4 == 0 && QL % 4 == 0 && F % 4 == 0 && CO % 4 == 0 && SU % 4 == 0 &&
                     SP2 % 4 == 0 && XLT % 4 == 0 && XLL % 4 == 0 && XLR % 4 == 0 && PBS % 4 == 0 &&
                     HBS % 4 == 0 && HRS % 4 == 0 && MB % 2 == 0,
                 "16-byte alignment of the vector and cp.async buffers");
   static_assert(CL * BAND == 128, "a cluster of CTAs covers the 128 rows of a tile");
+  static_assert(SU % 32 == 0 && SP2 % 32 == 0 && (BAND * BW) % 32 == 0 && OU % 32 == 0 && OP1 % 32 == 0,
+                "tensor copies need 128-byte aligned shared memory");
 };
+
+// tensor maps of the state arrays: u, f, p1 with 128 x 16 boxes, p2 with 132 x 16 boxes
+struct Mt4Maps {
+  CUtensorMap u, f, p1, p2;
+};
+
+__device__ __forceinline__ void tma_load_2d(float* dst, const CUtensorMap* map, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const float* src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(smem_addr(src))
+               : "memory");
+}
+__device__ __forceinline__ void tma_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void tma_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void tma_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void tma_fence_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ float lane4(f32x2 v, int h) { return h ? hi2(v) : lo2(v); }
 
-template <int FID, bool MASK>
-__device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const int first, const int stride) {
+template <int FID, bool MASK, bool TMA>
+__device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps* M, const int first,
+                                               const int stride) {
   using L = Mt4Layout;
   constexpr int NW = L::NW, CL = L::CL, BAND = L::BAND, NT = L::NT, BW = L::BW;
-  extern __shared__ __align__(16) float smem[];
+  extern __shared__ __align__(128) float smem[];
   float* sUB = smem + L::UB;
   float* sQ1 = smem + L::Q1;
   float* sCo = smem + L::CO;
-  const uint32_t mbU = smem_addr(smem + L::MB);
+  const uint32_t mbU = smem_addr(smem + (TMA ? L::MBT : L::MB));
   const uint32_t mbQ = mbU + 8;
+  const uint32_t mbL = mbU + 16;  // tensor loads of the staged subdomain (TMA)
 
   const Grid g = A.g;
   const int T = g.NR * g.NC;
@@ -109,6 +152,7 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const int fir
   if (tid == 0) {
     mbar_init(mbU, 1);
     mbar_init(mbQ, 1);
+    if (TMA) mbar_init(mbL, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int q = tid; q < 8 * min(K, L::kMaxSmemCoef); q += NT) sCo[q] = reinterpret_cast<const float*>(A.coef)[q];
@@ -124,21 +168,32 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const int fir
     const int a = t / g.NC, b = t - a * g.NC;
     const int c0 = b * 128;
     const int gb = a * 128 + rank * BAND;  // image row of the band's first row
+    if (TMA) {
+      if (tid == 0) {
+        mbar_arrive_expect_tx(mbL, L::kTmaBytes);
+        tma_load_2d(smem + L::SU, &M->u, c0, gb, mbL);
+        tma_load_2d(smem + L::SU + BAND * BW, &M->f, c0, gb, mbL);
+        tma_load_2d(smem + L::SU + 2 * BAND * BW, &M->p1, c0, gb + a, mbL);
+        tma_load_2d(smem + L::SP2, &M->p2, c0 + b - (b & 3), gb, mbL);
+      }
+    } else {
 #pragma unroll
-    for (int m = 0; m < 12; ++m) {  // u, f, p1: 3 x BAND rows x 32 chunks of 16 bytes
-      const int fld = m >> 2;
-      const int q = tid + NT * (m & 3);
-      const int row = q >> 5, ch = q & 31;
-      const float* base = fld == 0 ? A.u : (fld == 1 ? A.f : A.P1);
-      const int grow = gb + row + (fld == 2 ? a : 0);
-      cp_async16(smem + L::SU + fld * BAND * BW + row * BW + 4 * ch, base + (size_t)grow * g.W + c0 + 4 * ch);
-    }
+      for (int m = 0; m < 12; ++m) {  // u, f, p1: 3 x BAND rows x 32 chunks of 16 bytes
+        const int fld = m >> 2;
+        const int q = tid + NT * (m & 3);
+        const int row = q >> 5, ch = q & 31;
+        const float* base = fld == 0 ? A.u : (fld == 1 ? A.f : A.P1);
+        const int grow = gb + row + (fld == 2 ? a : 0);
+        cp_async16(smem + L::SU + fld * BAND * BW + row * BW + 4 * ch, base + (size_t)grow * g.W + c0 + 4 * ch);
+      }
 #pragma unroll
-    for (int m = 0; m < 5; ++m) {  // p2 window: BAND rows x 33 chunks
-      const int q = tid + NT * m;
-      if (q < BAND * 33) {
-        const int row = q / 33, ch = q - row * 33;
-        cp_async16(smem + L::SP2 + row * L::P2S + 4 * ch, A.P2 + (size_t)(gb + row) * W2 + c0 + b - (b & 3) + 4 * ch);
+      for (int m = 0; m < 5; ++m) {  // p2 window: BAND rows x 33 chunks
+        const int q = tid + NT * m;
+        if (q < BAND * 33) {
+          const int row = q / 33, ch = q - row * 33;
+          cp_async16(smem + L::SP2 + row * L::P2S + 4 * ch,
+                     A.P2 + (size_t)(gb + row) * W2 + c0 + b - (b & 3) + 4 * ch);
+        }
       }
     }
     if (tid < 32) {
@@ -173,8 +228,10 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const int fir
   };
 
   if (first < T) prefetch(first);
+  uint32_t nsub = 0;             // subdomains started (phase of mbL)
+  int pa = -1, pc0 = 0, pgb = 0;  // previous subdomain, whose u and p1 wait in the out-buffer (TMA)
 
-  for (int t = first; t < T; t += stride) {
+  for (int t = first; t < T; t += stride, ++nsub) {
     const int a = t / g.NC, b = t - a * g.NC;
     const int c0 = b * 128;
     const int gb = a * 128 + rank * BAND;
@@ -189,7 +246,13 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const int fir
     uint32_t in_d = 0;  // bit 4c + r: pixel (row r, column j0 + c) lies in the inpainting domain
 
     cp_async_wait_all();
+    if (TMA && !mbar_wait(mbL, nsub & 1)) timed_out = true;
     __syncthreads();  // staging landed; the previous subdomain's shared arrays are free
+    if (TMA && tid == 0 && pa >= 0) {  // the previous subdomain's u and p1 bands
+      tma_store_2d(&M->u, smem + L::OU, pc0, pgb);
+      tma_store_2d(&M->p1, smem + L::OP1, pc0, pgb + pa);
+      tma_commit();
+    }
     {
       f32x2 FV[4][2];
 #pragma unroll
@@ -385,6 +448,7 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const int fir
         *reinterpret_cast<float4*>(smem + L::PBS + j0) = make_float4(pB[0], pB[1], pB[2], pB[3]);
         *reinterpret_cast<float4*>(sQ1 + NW * BW + j0) = make_float4(qB[0], qB[1], qB[2], qB[3]);
       }
+      if (TMA && k == K - 1 && tid == 0) tma_wait_read();  // the out-buffer is free for this subdomain's bands
       __syncthreads();
     }
     if (need_qh) wait_q();  // drain the last pbar1 halo (not read)
@@ -393,10 +457,15 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const int fir
     for (int r = 0; r < 4; ++r) {
       const int e = r & 1, h = r >> 1;
       const int gi = gb + lr0 + r;
-      *reinterpret_cast<float4*>(A.u + (size_t)gi * g.W + c0 + j0) =
-          make_float4(lane4(U[0][e], h), lane4(U[1][e], h), lane4(U[2][e], h), lane4(U[3][e], h));
-      *reinterpret_cast<float4*>(A.P1 + (size_t)(gi + a) * g.W + c0 + j0) =
-          make_float4(lane4(P1[0][e], h), lane4(P1[1][e], h), lane4(P1[2][e], h), lane4(P1[3][e], h));
+      const float4 uv = make_float4(lane4(U[0][e], h), lane4(U[1][e], h), lane4(U[2][e], h), lane4(U[3][e], h));
+      const float4 pv = make_float4(lane4(P1[0][e], h), lane4(P1[1][e], h), lane4(P1[2][e], h), lane4(P1[3][e], h));
+      if (TMA) {
+        *reinterpret_cast<float4*>(smem + L::OU + (lr0 + r) * BW + j0) = uv;
+        *reinterpret_cast<float4*>(smem + L::OP1 + (lr0 + r) * BW + j0) = pv;
+      } else {
+        *reinterpret_cast<float4*>(A.u + (size_t)gi * g.W + c0 + j0) = uv;
+        *reinterpret_cast<float4*>(A.P1 + (size_t)(gi + a) * g.W + c0 + j0) = pv;
+      }
       float* p2row = A.P2 + (size_t)gi * W2 + c0 + b + j0;
 #pragma unroll
       for (int c = 0; c < 4; ++c) p2row[c] = lane4(P2[c][e], h);
@@ -415,7 +484,22 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const int fir
       *reinterpret_cast<float4*>(A.P1 + (size_t)(a * 128 + 128 + a) * g.W + c0 + j0) = v;
       *reinterpret_cast<float4*>(A.out.SB + (size_t)a * g.W + c0 + j0) = v;
     }
+    if (TMA) {
+      tma_fence_smem();  // the out-buffer writes become visible to the tensor stores
+      pa = a;
+      pc0 = c0;
+      pgb = gb;
+    }
   }
+  if (TMA && pa >= 0) {  // the last subdomain's bands
+    __syncthreads();
+    if (tid == 0) {
+      tma_store_2d(&M->u, smem + L::OU, pc0, pgb);
+      tma_store_2d(&M->p1, smem + L::OP1, pc0, pgb + pa);
+      tma_commit();
+    }
+  }
+  if (TMA && tid == 0) tma_wait_all();  // the stores are complete before the CTA's shared memory is released
   cp_async_wait_all();
   cluster_arrive<true>();  // no CTA leaves while a neighbour may still write into it
   cluster_wait();
@@ -424,20 +508,25 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const int fir
 
 template <int FID, bool MASK>
 __global__ void __launch_bounds__(Mt4Layout::NT, 3) k_fused_mt4(const LocalArgs A) {
-  fused_mt4_body<FID, MASK>(A, blockIdx.y, gridDim.y);
+  fused_mt4_body<FID, MASK, false>(A, nullptr, blockIdx.y, gridDim.y);
 }
 
 template <int FID, bool MASK>
-int& mt4_clusters(int dev) {
-  static int n[64] = {0};
-  return n[dev & 63];
+__global__ void __launch_bounds__(Mt4Layout::NT, 3) k_fused_mt4t(const LocalArgs A, const __grid_constant__ Mt4Maps M) {
+  fused_mt4_body<FID, MASK, true>(A, &M, blockIdx.y, gridDim.y);
 }
 
-cudaLaunchConfig_t mt4_config(int clusters, cudaLaunchAttribute* attr) {
+// clusters of each kernel resident at once, per device: [TMA][FID * 2 + MASK]
+int& mt4_clusters(int dev, bool tma, int fid, bool mask) {
+  static int n[64][2][6] = {};
+  return n[dev & 63][tma ? 1 : 0][fid * 2 + (mask ? 1 : 0)];
+}
+
+cudaLaunchConfig_t mt4_config(int clusters, bool tma, cudaLaunchAttribute* attr) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(Mt4Layout::CL, clusters, 1);
   cfg.blockDim = dim3(Mt4Layout::NT, 1, 1);
-  cfg.dynamicSmemBytes = Mt4Layout::BYTES;
+  cfg.dynamicSmemBytes = tma ? Mt4Layout::BYTES_TMA : Mt4Layout::BYTES;
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = Mt4Layout::CL;
   attr[0].val.clusterDim.y = 1;
@@ -447,13 +536,13 @@ cudaLaunchConfig_t mt4_config(int clusters, cudaLaunchAttribute* attr) {
   return cfg;
 }
 
-template <int FID, bool MASK>
-cudaError_t prepare_mt4_one() {
-  auto kern = k_fused_mt4<FID, MASK>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Mt4Layout::BYTES);
+template <class Kern>
+cudaError_t prepare_kernel(Kern kern, bool tma, int fid, bool mask) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(tma ? Mt4Layout::BYTES_TMA : Mt4Layout::BYTES));
   if (e != cudaSuccess) return e;
   cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t cfg = mt4_config(1024, attr);
+  cudaLaunchConfig_t cfg = mt4_config(1024, tma, attr);
   int n = 0;
   if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
     cudaGetLastError();
@@ -461,21 +550,80 @@ cudaError_t prepare_mt4_one() {
   }
   int dev = 0;
   cudaGetDevice(&dev);
-  mt4_clusters<FID, MASK>(dev) = n;
+  mt4_clusters(dev, tma, fid, mask) = n;
   return cudaSuccess;
 }
 
 template <int FID, bool MASK>
-cudaError_t launch_mt4_one(const LocalArgs& a, cudaStream_t st) {
+cudaError_t prepare_mt4_one() {
+  cudaError_t e = prepare_kernel(k_fused_mt4<FID, MASK>, false, FID, MASK);
+  if (e != cudaSuccess) return e;
+  return prepare_kernel(k_fused_mt4t<FID, MASK>, true, FID, MASK);
+}
+
+int mt4_grid(const LocalArgs& a, bool tma, int fid, bool mask) {
   int dev = 0;
   cudaGetDevice(&dev);
   const int tiles = a.g.NR * a.g.NC;
-  int nc = mt4_clusters<FID, MASK>(dev);
-  if (nc <= 0 || nc > tiles) nc = tiles;
+  int nc = mt4_clusters(dev, tma, fid, mask);
+  return (nc <= 0 || nc > tiles) ? tiles : nc;
+}
+
+template <int FID, bool MASK>
+cudaError_t launch_mt4_one(const LocalArgs& a, cudaStream_t st) {
   cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t cfg = mt4_config(nc, attr);
+  cudaLaunchConfig_t cfg = mt4_config(mt4_grid(a, false, FID, MASK), false, attr);
   cfg.stream = st;
   return cudaLaunchKernelEx(&cfg, k_fused_mt4<FID, MASK>, a);
+}
+
+template <int FID, bool MASK>
+cudaError_t launch_mt4t_one(const LocalArgs& a, const Mt4Maps& maps, cudaStream_t st) {
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = mt4_config(mt4_grid(a, true, FID, MASK), true, attr);
+  cfg.stream = st;
+  return cudaLaunchKernelEx(&cfg, k_fused_mt4t<FID, MASK>, a, maps);
+}
+
+// cuTensorMapEncodeTiled from the driver (no link-time dependency on libcuda)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2-D float32 map of a rows x cols array (row pitch = cols) with boxes of box_cols x 16
+bool encode_map(CUtensorMap* m, const void* base, uint64_t cols, uint64_t rows, uint32_t box_cols) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dim[2] = {cols, rows};
+  const cuuint64_t stride[1] = {cols * sizeof(float)};
+  const cuuint32_t box[2] = {box_cols, (cuuint32_t)Mt4Layout::BAND};
+  const cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dim, stride, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool encode_maps(const LocalArgs& a, Mt4Maps* m) {
+  const Grid& g = a.g;
+  return encode_map(&m->u, a.u, g.W, g.H, 128) && encode_map(&m->f, a.f, g.W, g.H, 128) &&
+         encode_map(&m->p1, a.P1, g.W, g.H + g.NR, 128) &&
+         encode_map(&m->p2, a.P2, g.W + g.NC, g.H, Mt4Layout::P2S);
 }
 
 }  // namespace
@@ -495,8 +643,16 @@ cudaError_t fused_mt4_prepare() {
   return prepare_mt4_one<FID_SEG, false>();
 }
 
-cudaError_t launch_fused_mt4(const LocalArgs& a, int fid, cudaStream_t st) {
+cudaError_t launch_fused_mt4(const LocalArgs& a, int fid, bool tma, cudaStream_t st) {
   const bool m = a.mask != nullptr;
+  Mt4Maps maps;
+  if (tma && encode_maps(a, &maps)) {
+    switch (fid) {
+      case FID_L2: return m ? launch_mt4t_one<FID_L2, true>(a, maps, st) : launch_mt4t_one<FID_L2, false>(a, maps, st);
+      case FID_L1: return m ? launch_mt4t_one<FID_L1, true>(a, maps, st) : launch_mt4t_one<FID_L1, false>(a, maps, st);
+      default: return launch_mt4t_one<FID_SEG, false>(a, maps, st);
+    }
+  }
   switch (fid) {
     case FID_L2: return m ? launch_mt4_one<FID_L2, true>(a, st) : launch_mt4_one<FID_L2, false>(a, st);
     case FID_L1: return m ? launch_mt4_one<FID_L1, true>(a, st) : launch_mt4_one<FID_L1, false>(a, st);
