@@ -675,7 +675,10 @@ __global__ void __launch_bounds__(128 * TR, MINB) k_adj_full(const LocalArgs A, 
   // the right side, sQ1 = a_t of each thread row's first p1 row, row TR from below)
   float Au[R], AP1[R], AP2[R], AQ1[R], AQ2[R], AH1[R], AH2[R], Afr[R];
   float APB = 0.f, AQB = 0.f, AHB = 0.f;
-  double acc = 0.0;
+  // the thread's share of dL/dalpha: compensated float32 sum (Kahan) over its pixels and
+  // the K reverse iterations, then float64 across threads (a float64 operation per pixel
+  // and iteration made this kernel wait on the slow float64 pipe)
+  float acc_s = 0.f, acc_c = 0.f;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int gi = r0 + i0 + r;
@@ -737,7 +740,12 @@ __global__ void __launch_bounds__(128 * TR, MINB) k_adj_full(const LocalArgs A, 
       Ad[r] = c.sig * aub;
       sUr[r * L::US] = Ad[r];
       if (df != 0.0f) Afr[r] += df * aun;
-      acc += (double)dal * (double)aun;
+      {
+        const float y = dal * aun - acc_c;
+        const float tsum = acc_s + y;
+        acc_c = (tsum - acc_s) - y;
+        acc_s = tsum;
+      }
       if (rr == 0 && push_down) st_async_f32(remote_u, Ad[R - 1], remote_mbU);
     }
     __syncthreads();
@@ -797,6 +805,7 @@ __global__ void __launch_bounds__(128 * TR, MINB) k_adj_full(const LocalArgs A, 
     Z.AP2[e] = sPR[lr0 + j];
     Z.APh2[e] = sXR[lr0 + j];
   }
+  double acc = (double)acc_s - (double)acc_c;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   __shared__ double sw[NT / 32];

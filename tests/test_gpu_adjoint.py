@@ -130,6 +130,20 @@ def test_adjoint_checkpoint_spacing_and_path_do_not_change_bits(cuda_lib):
         assert ga == base[2], (every, path)
 
 
+def test_full_tile_reverse_kernel_against_plain_path(cuda_lib):
+    """With 128 x 128 subdomains the fused path runs the full-tile reverse kernel, which
+    sums its share of dL/dalpha in compensated float32 per thread (float64 across
+    threads); the plain path sums in float64 per pixel.  dL/df is bit-identical, dL/dalpha
+    agrees to 1e-6 relative."""
+    f, g, _ = _case(256, 256, "l2", 0.0, seed=7)
+    N = 6
+    u1, gf1, ga1 = _gpu(f, g, None, 2, 2, N, "l2", every=3, path="fused")
+    u2, gf2, ga2 = _gpu(f, g, None, 2, 2, N, "l2", every=3, path="plain")
+    assert np.array_equal(u1, u2)
+    assert np.array_equal(gf1, gf2)
+    assert ga2 != 0.0 and abs(ga1 - ga2) <= 1e-6 * abs(ga2), (ga1, ga2)
+
+
 def test_adjoint_backward_repeats_and_profiling_mode(cuda_lib):
     """A second backward on the same checkpoints (graph replay) and a backward with the
     measurement hooks on (direct launches) give the bits of the first one."""
