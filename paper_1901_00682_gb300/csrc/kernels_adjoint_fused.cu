@@ -293,7 +293,9 @@ __global__ void __launch_bounds__(BW* TR, MINB) k_adj_fused(const LocalArgs A, c
   // row of every thread row / of the band below.
   float Au[R], AP1[R], AP2[R], AQ1[R], AQ2[R], AH1[R], AH2[R], Afr[R];
   float APB = 0.f, AQB = 0.f, AHB = 0.f, atB = 0.f;
-  double acc = 0.0;
+  // the thread's share of dL/dalpha: compensated float32 sum (Kahan), float64 across
+  // threads (a float64 add per pixel and iteration keeps the slow float64 pipe busy)
+  float acc_s = 0.f, acc_c = 0.f;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int i = i0 + r;
@@ -378,7 +380,12 @@ __global__ void __launch_bounds__(BW* TR, MINB) k_adj_fused(const LocalArgs A, c
       Ad[r] = c.sig * aub;
       sU[lr * L::US + j + 1] = Ad[r];
       if (df != 0.0f) Afr[r] += df * aun;
-      if (col_ok && i0 + r < mr) acc += (double)dal * (double)aun;
+      if (col_ok && i0 + r < mr) {
+        const float y = dal * aun - acc_c;
+        const float tsum = acc_s + y;
+        acc_c = (tsum - acc_s) - y;
+        acc_s = tsum;
+      }
     };
     if (CL > 1) cl_wait();
     ru_px(R - 1);
@@ -453,6 +460,7 @@ __global__ void __launch_bounds__(BW* TR, MINB) k_adj_fused(const LocalArgs A, c
       Z.APh2[e2 + 1] = sXR[lr0 + r];
     }
   }
+  double acc = (double)acc_s - (double)acc_c;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   __shared__ double sw[NT / 32];

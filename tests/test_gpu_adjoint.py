@@ -119,7 +119,10 @@ def test_adjoint_l1_matches_fp64_autograd(cuda_lib):
 
 def test_adjoint_checkpoint_spacing_and_path_do_not_change_bits(cuda_lib):
     """Recomputation is deterministic and the fused and plain paths run the same
-    arithmetic, so the gradient does not depend on the checkpoint spacing or path."""
+    arithmetic, so the gradient does not depend on the checkpoint spacing or path: u
+    and dL/df bit for bit; dL/dalpha bit for bit across checkpoint spacings, and to 1e-6
+    relative between the paths (the fused reverse kernels sum each thread's share in
+    compensated float32, the plain path every pixel's term in float64)."""
     f, g, mask = _case(64, 48, "l2", 0.0, seed=5)
     N = 9
     base = _gpu(f, g, None, 2, 3, N, "l2", every=1)
@@ -127,7 +130,10 @@ def test_adjoint_checkpoint_spacing_and_path_do_not_change_bits(cuda_lib):
         u, gf, ga = _gpu(f, g, None, 2, 3, N, "l2", every=every, path=path)
         assert np.array_equal(u, base[0]), (every, path)
         assert np.array_equal(gf, base[1]), (every, path)
-        assert ga == base[2], (every, path)
+        if path == "fused":
+            assert ga == base[2], (every, path)
+        else:
+            assert abs(ga - base[2]) <= 1e-6 * abs(base[2]), (every, path, ga, base[2])
 
 
 def test_full_tile_reverse_kernel_against_plain_path(cuda_lib):
