@@ -205,6 +205,19 @@ int dd_tv_current_energy(dd_tv* h, double* J_out);
 int dd_tv_set_profiling(dd_tv* h, int on);
 int dd_tv_profile_read(dd_tv* h, double* ms, long long* launches);
 
+/* ---- Failure-detection hook (no counterpart in the paper). ----
+ * Every wait of the fused kernels on a halo or a copy (an mbarrier phase) is bounded
+ * (about a second); when the bound runs out the kernel sets the handle's device status
+ * word and finishes, and the next call that synchronises returns DD_TV_ETIMEOUT.
+ * dd_tv_fault_probe makes that happen on purpose without a fault: kind 0 launches one
+ * thread that waits, with the same bounded wait, on an mbarrier phase that nothing
+ * completes (no copy is counted on it); kind 1 writes the status word from the host,
+ * as a corrupted word would read.  Either way the call then reads the word as the
+ * solver does and returns DD_TV_ETIMEOUT (message in dd_tv_last_error), the word is
+ * cleared and the handle stays usable.  *waited_ms (may be NULL) receives the device
+ * time the kind-0 wait took (0 for kind 1).  Other kinds: DD_TV_EINVAL. */
+int dd_tv_fault_probe(dd_tv* h, int kind, double* waited_ms);
+
 /* Measures the shared-memory load bandwidth of the current device (bytes per second
  * summed over all SMs) with a streaming ld.shared loop, for use as the roofline
  * denominator of the fused local solver.  Synchronous; allocates and frees its own

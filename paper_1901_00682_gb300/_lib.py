@@ -84,6 +84,7 @@ SIGNATURES = {
     "dd_tv_adjoint_backward": (_i, [_vp, _vp, _vp, _DP]),
     "dd_tv_adjoint_release": (_i, [_vp]),
     "dd_tv_set_alpha": (_i, [_vp, _d]),
+    "dd_tv_fault_probe": (_i, [_vp, _i, _DP]),
 }
 
 _lock = threading.Lock()
@@ -301,6 +302,15 @@ class Solver:
         J, D = ctypes.c_double(), ctypes.c_double()
         check(self.lib.dd_tv_gap(self.h, ctypes.byref(J), ctypes.byref(D)), self.h)
         return J.value, D.value
+
+    def fault_probe(self, kind: int):
+        """Forces the timeout path (kind 0: a bounded device wait that runs out; kind 1:
+        the status word set from the host).  Returns (status code, message, device ms
+        of the wait); DD_TV_ETIMEOUT is the expected code."""
+        ms = ctypes.c_double()
+        rc = self.lib.dd_tv_fault_probe(self.h, int(kind), ctypes.byref(ms))
+        msg = self.lib.dd_tv_last_error(self.h)
+        return rc, (msg.decode() if msg else ""), ms.value
 
     def set_alpha(self, alpha: float):
         check(self.lib.dd_tv_set_alpha(self.h, float(alpha)), self.h)

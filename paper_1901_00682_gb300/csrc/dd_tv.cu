@@ -1114,4 +1114,26 @@ int dd_tv_profile_read(dd_tv* h, double* ms, long long* launches) {
   return DD_TV_OK;
 }
 
+int dd_tv_fault_probe(dd_tv* h, int kind, double* waited_ms) {
+  if (!h) return DD_TV_EINVAL;
+  if (waited_ms) *waited_ms = 0.0;
+  if (kind == 0) {
+    unsigned long long* d_ns = nullptr;
+    CK(cudaMalloc((void**)&d_ns, sizeof(*d_ns)));
+    unsigned long long ns = 0;
+    cudaError_t e = launch_wait_probe(h->flag, d_ns, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ns, d_ns, sizeof(ns), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d_ns);
+    if (e != cudaSuccess) return fail(h, DD_TV_ECUDA, "wait probe: %s", cudaGetErrorString(e));
+    if (waited_ms) *waited_ms = (double)ns * 1e-6;
+  } else if (kind == 1) {
+    const int one = 1;
+    CK(cudaMemcpyAsync(h->flag, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  } else {
+    return fail(h, DD_TV_EINVAL, "fault probe kind must be 0 (device wait) or 1 (status word)");
+  }
+  return check_timeout(h);
+}
+
 }  // extern "C"

@@ -213,5 +213,8 @@ int adj_alpha_slots_fused(const Grid& g);
 // ---- kernels_misc.cu
 // u0 = f (0 on D) for L2/L1, 1/2 for SEG
 cudaError_t launch_init_u(const Grid& g, int fidelity, const float* f, const uint8_t* mask, float* u, cudaStream_t st);
+// one bounded mbarrier wait that runs out (nothing completes the phase): sets *err,
+// writes the device time it took (ns) to *waited_ns
+cudaError_t launch_wait_probe(int* err, unsigned long long* waited_ns, cudaStream_t st);
 // global field (H+1) x W / H x (W+1) <-> torn field with a 1 x 1 grid (same arrays)
 }  // namespace ddtv

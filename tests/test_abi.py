@@ -88,3 +88,4 @@ def test_null_handle_calls_are_safe(lib):
     assert lib.dd_tv_destroy(None) == _lib.OK
     assert lib.dd_tv_iterate(None, 1) == _lib.EINVAL
     assert lib.dd_tv_outer_count(None) == -1
+    assert lib.dd_tv_fault_probe(None, 0, None) == _lib.EINVAL
