@@ -132,6 +132,9 @@ int validate(const dd_tv_params* p, char* msg, size_t len) {
   if (p->path != DD_TV_PATH_FULLDIM) {
     if (p->sub_rows < 1 || p->sub_rows > p->height) return BAD("sub_rows must be in [1, height] (got %d)", p->sub_rows);
     if (p->sub_cols < 1 || p->sub_cols > p->width) return BAD("sub_cols must be in [1, width] (got %d)", p->sub_cols);
+    // the interface kernels number the edges in 32-bit integers
+    const long long edges = (long long)(p->sub_rows - 1) * p->width + (long long)(p->sub_cols - 1) * p->height;
+    if (edges > (1LL << 30) - 1) return BAD("too many interface edges (%lld > 2^30 - 1): use fewer subdomains", edges);
   }
   if (p->fidelity < DD_TV_L2 || p->fidelity > DD_TV_SEG) return BAD("unknown fidelity %d", p->fidelity);
   if (!(p->alpha > 0.0) || !std::isfinite(p->alpha)) return BAD("alpha must be finite and > 0");
@@ -473,6 +476,8 @@ void adj_free(AdjointWork* w) {
 // slots to nck checkpoints and m segment states.
 int adj_reserve(dd_tv* h, int nck, int m) {
   if (!h->adj) {
+    if (std::max(adj_alpha_slots(h->g), adj_alpha_slots_fused(h->g)) > (1LL << 30))
+      return fail(h, DD_TV_EUNSUPPORTED, "too many subdomains for the reverse pass");
     AdjointWork* w = new (std::nothrow) AdjointWork();
     if (!w) return fail(h, DD_TV_ENOMEM, "out of host memory");
     h->adj = w;
@@ -481,7 +486,7 @@ int adj_reserve(dd_tv* h, int nck, int m) {
     const size_t tape_f = adj_fused_tape_floats(h->g, h->p.inner_iters);
     // the fused reverse kernel keeps a per-CTA tape; beyond 4 GiB use the per-step path
     w->fused = tape_f > 0 && tape_f * sizeof(float) <= (4ull << 30);
-    w->nal = std::max(adj_alpha_slots(h->g), adj_alpha_slots_fused(h->g));
+    w->nal = (int)std::max(adj_alpha_slots(h->g), adj_alpha_slots_fused(h->g));
     if (w->fused) CK(adj_fused_prepare());
     int rc;
     if ((rc = dalloc(h, &w->Au, h->npx)) || (rc = dalloc(h, &w->Ad, h->npx)) || (rc = dalloc(h, &w->Af, h->npx)) ||

@@ -195,7 +195,7 @@ cudaError_t launch_sum_f64(const double* x, long long n, double* partials, unsig
                            cudaStream_t st);
 int sum_f64_partials_count();
 // number of float64 partial sums the reverse u-kernel keeps for an image grid
-int adj_alpha_slots(const Grid& g);
+long long adj_alpha_slots(const Grid& g);
 
 // ---- kernels_adjoint_fused.cu
 // Reverse of one outer iteration's local solves, tape in shared memory: a = the local
@@ -208,7 +208,7 @@ size_t adj_fused_tape_floats(const Grid& g, int K);
 // shared-memory opt-in of the fused reverse kernels (outside any stream capture)
 cudaError_t adj_fused_prepare();
 // alpha partial-sum slots the fused reverse kernel uses
-int adj_alpha_slots_fused(const Grid& g);
+long long adj_alpha_slots_fused(const Grid& g);
 
 // ---- kernels_misc.cu
 // u0 = f (0 on D) for L2/L1, 1/2 for SEG

@@ -400,9 +400,9 @@ cudaError_t launch_adj_initial(const AdjArgs& r, cudaStream_t st) {
 
 int sum_f64_partials_count() { return kSumBlocks; }
 
-int adj_alpha_slots(const Grid& g) {
+long long adj_alpha_slots(const Grid& g) {
   const dim3 d = pixel_grid(g);
-  return (int)(d.x * d.y);
+  return (long long)d.x * d.y;
 }
 
 cudaError_t launch_sum_f64(const double* x, long long n, double* partials, unsigned int* counter, double* out,

@@ -935,7 +935,7 @@ int adj_pick(int mr, int mc) {
 
 }  // namespace
 
-int adj_alpha_slots_fused(const Grid& g) { return g.NR * g.NC * 8; }
+long long adj_alpha_slots_fused(const Grid& g) { return (long long)g.NR * g.NC * 8; }
 
 size_t adj_fused_tape_floats(const Grid& g, int K) {
   const int mr = (g.H + g.NR - 1) / g.NR, mc = (g.W + g.NC - 1) / g.NC;

@@ -89,3 +89,14 @@ def test_null_handle_calls_are_safe(lib):
     assert lib.dd_tv_iterate(None, 1) == _lib.EINVAL
     assert lib.dd_tv_outer_count(None) == -1
     assert lib.dd_tv_fault_probe(None, 0, None) == _lib.EINVAL
+
+
+def test_create_rejects_edge_counts_beyond_32_bit_numbering(lib):
+    """The interface kernels number the edges in 32-bit integers: (N_r - 1) W + (N_c - 1) H
+    must stay below 2^30 (here exactly 2^30), refused before any device call."""
+    from paper_1901_00682_gb300 import _lib
+    p = _lib.make_params(32768, 32768, 16385, 16385)
+    h = ctypes.c_void_p()
+    rc = lib.dd_tv_create(ctypes.byref(h), ctypes.byref(p))
+    assert rc == _lib.EINVAL and not h.value
+    assert "interface edges" in lib.dd_tv_last_error(None).decode()

@@ -40,7 +40,8 @@ def test_timeout_path_reports_and_handle_recovers(kind):
     assert rc == L.ETIMEOUT, (rc, msg)
     assert "wait" in msg
     if kind == 0:
-        assert 0.0 < waited < 10_000.0   # the bound is about a second
+        print(f"bounded wait ran out after {waited:.1f} ms of device time")
+        assert 0.0 < waited < 10_000.0
     else:
         assert waited == 0.0
     # the word was cleared: the handle solves, and exactly as a fresh one does

@@ -219,6 +219,46 @@ def test_full_size_4096_sampled_parity():
     assert np.abs(g["lamh"] - o.lamh).max() <= 1e-3
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("side", [46080, 46336])
+def test_maximum_size_sampled_subdomains(side):
+    """The largest square images the interface accepts with 128 x 128 subdomains (about
+    2^31 pixels).  At 46080^2 (360 x 360 subdomains, W + N_c a multiple of 4) the
+    default tensor-copy kernel runs; at 46336^2 the 2 x 4 micro-tile kernel runs and the
+    torn arrays P1, P2 hold more than 2^31 values.  After 2 outer iterations, sampled
+    subdomains (the four corners and an interior one) are compared element by element
+    with the oracle run on the subdomain and the two rings of subdomains around it: after
+    n outer iterations a subdomain depends on the subdomains fewer than n steps away, and
+    their local problems on which of their own neighbours exist, so a radius-n block of
+    subdomains reproduces its trajectory exactly."""
+    L = _gpu()
+    base = torch.from_numpy(synth.rof_image(4096, 4096, 400, 0.1, 0)[0]).cuda()
+    reps = -(-side // 4096)
+    big = base.repeat(reps, reps)
+    fd = big[:side, :side].contiguous()
+    del big, base
+    NT, n_outer = side // 128, 2
+    kw = dict(fidelity="l2", alpha=8.0, inner_iters=10)
+    with L.Solver(L.make_params(side, side, NT, NT, outer_iters=n_outer, **kw)) as s:
+        s.load(fd, None)
+        s.iterate(n_outer)
+        st = s.get_state()
+        torch.cuda.synchronize()
+    for a, b in [(0, 0), (0, NT - 1), (NT - 1, 0), (NT - 1, NT - 1), (NT // 2, NT // 3)]:
+        r0, r1, c0, c1 = max(0, a - n_outer), min(NT, a + n_outer + 1), max(0, b - n_outer), min(NT, b + n_outer + 1)
+        fs = fd[r0 * 128:r1 * 128, c0 * 128:c1 * 128].cpu().numpy()
+        _, o = _run_oracle(fs, None, n_outer, sub_rows=r1 - r0, sub_cols=c1 - c0, **kw)
+        ug = st["u"][a * 128:(a + 1) * 128, b * 128:(b + 1) * 128].cpu().numpy().astype(np.float64)
+        uo = o.u[(a - r0) * 128:(a - r0 + 1) * 128, (b - c0) * 128:(b - c0 + 1) * 128]
+        assert np.abs(ug - uo).max() <= U_TOL, (a, b)
+        # the subdomain's p1 dofs: rows a*129 .. a*129 + 128 of the torn layout
+        pg = st["P1"][a * 129:(a + 1) * 129, b * 128:(b + 1) * 128].cpu().numpy().astype(np.float64)
+        po = o.P1[(a - r0) * 129:(a - r0 + 1) * 129, (b - c0) * 128:(b - c0 + 1) * 128]
+        assert np.abs(pg - po).max() <= 1e-2, (a, b)
+    del st, fd
+    torch.cuda.empty_cache()
+
+
 N_VARIANTS = 16  # hardware mappings of a 128 x 128 subdomain (dd_tv_params.variant)
 
 

@@ -250,3 +250,38 @@ def test_forced_counts_reproduce_fixed_and_adaptive_runs():
     d = oracle.dd_run(pr, f, 5, counts=c.inner_counts, record=True)
     assert np.array_equal(c.u, d.u) and np.array_equal(c.inner_counts, d.inner_counts)
     assert c.inner_counts.min() < 30  # the rule did stop some solves early
+
+
+@pytest.mark.parametrize("n_outer", [1, 2, 3])
+def test_locality_of_the_outer_iteration(n_outer):
+    """Algorithm 1 starts from p~ = 0, lambda = 0, so the first local solves see only their
+    own f, and each further outer iteration couples a subdomain to its side neighbours
+    through lambda alone.  After n outer iterations a subdomain therefore depends on the
+    subdomains fewer than n steps away, whose local problems depend on which of their own
+    neighbours exist: the block of subdomains within n steps (clipped at the image border)
+    reproduces the subdomain's u and p exactly.  (This is what makes sampled comparisons
+    at sizes beyond the oracle's reach exact.)  The bound is sufficient, not always
+    necessary: inside one local solve information moves about a pixel per inner
+    iteration, so a smaller block can agree too.  The subdomain alone never does: its
+    sides turn from interface dofs into pinned image-border edges."""
+    T, m = 9, 8   # 9 x 9 subdomains of 8 x 8
+    f, _ = synth.rof_image(T * m, T * m, 30, 0.1, 11)
+    f = f.astype(np.float64)
+    kw = dict(fidelity="l2", alpha=6.0, tau=50.0, inner=5)
+    full = oracle.dd_run(oracle.Problem(T * m, T * m, T, T, **kw), f, n_outer)
+
+    def block(a, b, rad):
+        r0, r1, c0, c1 = max(0, a - rad), min(T, a + rad + 1), max(0, b - rad), min(T, b + rad + 1)
+        st = oracle.dd_run(oracle.Problem((r1 - r0) * m, (c1 - c0) * m, r1 - r0, c1 - c0, **kw),
+                           f[r0 * m:r1 * m, c0 * m:c1 * m], n_outer)
+        u = st.u[(a - r0) * m:(a - r0 + 1) * m, (b - c0) * m:(b - c0 + 1) * m]
+        p1 = st.P1[(a - r0) * (m + 1):(a - r0 + 1) * (m + 1), (b - c0) * m:(b - c0 + 1) * m]
+        return u, p1
+
+    for a, b in [(4, 4), (0, 0), (0, 4), (8, 3)]:
+        u_ref = full.u[a * m:(a + 1) * m, b * m:(b + 1) * m]
+        p_ref = full.P1[a * (m + 1):(a + 1) * (m + 1), b * m:(b + 1) * m]
+        u, p1 = block(a, b, n_outer)
+        assert np.array_equal(u, u_ref) and np.array_equal(p1, p_ref), (a, b)
+        u_alone, _ = block(a, b, 0)
+        assert np.abs(u_alone - u_ref).max() > 1e-3
