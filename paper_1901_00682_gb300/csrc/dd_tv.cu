@@ -247,9 +247,6 @@ struct PhaseMark {
 cudaError_t outer_once(dd_tv* h, int par) {
   cudaError_t e;
   const cudaStream_t st = h->stream;
-  // programmatic launches let each kernel's launch overlap the end of the one before;
-  // the measurement hooks bracket every phase with events and launch them plainly
-  const bool pdl = !h->prof && h->p.path == DD_TV_PATH_FUSED;
   if (h->p.path == DD_TV_PATH_FULLDIM) {
     LocalArgs a = local_args(h, 0);
     PhaseMark m(h, 1, 2 * a.K);
@@ -262,14 +259,14 @@ cudaError_t outer_once(dd_tv* h, int par) {
   }
   {
     PhaseMark m(h, 0, (h->nh + h->nv) ? 1 : 0);
-    if ((e = launch_interface(h->g, (float)h->p.sigma, h->strips[par], h->strips[1 - par], h->lamh, h->lamv, st,
-                              pdl)) != cudaSuccess)
+    if ((e = launch_interface(h->g, (float)h->p.sigma, h->strips[par], h->strips[1 - par], h->lamh, h->lamv, st)) !=
+        cudaSuccess)
       return e;
   }
   LocalArgs a = local_args(h, 1 - par);
   if (h->p.path == DD_TV_PATH_FUSED) {
     PhaseMark m(h, 1, 1);
-    return launch_fused_local(a, h->fid, h->p.variant, st, pdl);
+    return launch_fused_local(a, h->fid, h->p.variant, st);
   }
   PhaseMark m(h, 1, 1 + 2 * a.K + ((h->nh + h->nv) ? 1 : 0));
   if ((e = launch_plain_phat(a, h->Ph1, h->Ph2, h->Pb1, h->Pb2, st)) != cudaSuccess) return e;

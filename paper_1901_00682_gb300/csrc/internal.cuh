@@ -89,10 +89,8 @@ struct AdjArgs {
 
 // ---- kernels_interface.cu
 // lambda += sigma ((2 cur_s - prev_s) - (2 cur_t - prev_t)) on every interface edge.
-// pdl: launched with programmatic stream serialisation (it may start while the local
-// solves before it finish; it waits for them before reading the strips).
 cudaError_t launch_interface(const Grid& g, float sigma, Strips cur, Strips prev, float* lamh, float* lamv,
-                             cudaStream_t st, bool pdl = false);
+                             cudaStream_t st);
 // strips <- interface values of the torn field (P1, P2)
 cudaError_t launch_extract_strips(const Grid& g, const float* P1, const float* P2, Strips s, cudaStream_t st);
 // P1/P2 <- 0 except the interface values, taken from the strips
@@ -105,9 +103,7 @@ cudaError_t launch_interface_batch(const BatchIfaceArgs& a, int total4, cudaStre
 cudaError_t launch_fused_batch(const BatchArgs& B, int total_tiles, int variant, cudaStream_t st);
 // One outer iteration's local solves, all tiles, fused (returns cudaErrorInvalidValue
 // if no fused configuration fits the tile shape).
-// pdl: the default kernel is launched with programmatic stream serialisation (its
-// prologue overlaps the multiplier update, which it waits for before any state access).
-cudaError_t launch_fused_local(const LocalArgs& a, int fidelity, int variant, cudaStream_t st, bool pdl = false);
+cudaError_t launch_fused_local(const LocalArgs& a, int fidelity, int variant, cudaStream_t st);
 // Sets the shared-memory opt-in of every fused configuration on the current device
 // (called at handle creation, outside any stream capture).
 cudaError_t fused_prepare();
@@ -155,7 +151,7 @@ cudaError_t fused_ps_prepare();
 bool fused_mt4_supported(const LocalArgs& a);
 // tma: move the state with tensor copies (falls back to cp.async if the tensor maps
 // cannot be encoded)
-cudaError_t launch_fused_mt4(const LocalArgs& a, int fidelity, bool tma, cudaStream_t st, bool pdl = false);
+cudaError_t launch_fused_mt4(const LocalArgs& a, int fidelity, bool tma, cudaStream_t st);
 cudaError_t fused_mt4_prepare();
 
 // ---- kernels_plain.cu

@@ -2134,14 +2134,14 @@ cudaError_t launch_fused_batch(const BatchArgs& B, int total_tiles, int variant,
   return launch_fused_mt_batch(B, total_tiles, st);
 }
 
-cudaError_t launch_fused_local(const LocalArgs& a, int fid, int variant, cudaStream_t st, bool pdl) {
+cudaError_t launch_fused_local(const LocalArgs& a, int fid, int variant, cudaStream_t st) {
   // largest tile of the (ragged) partition
   const int mr = (a.g.H + a.g.NR - 1) / a.g.NR, mc = (a.g.W + a.g.NC - 1) / a.g.NC;
   if (a.inner_tol2 > 0.0) variant = 0;  // adaptive stopping: the cluster-barrier kernel only
   if (a.inner_tol2 <= 0.0 && a.g.H == 128 * a.g.NR && a.g.W == 128 * a.g.NC) {  // every tile exactly 128 x 128
     switch (variant) {
       case 0:  // default: persistent, 4 x 4 micro-tiles, one warp per thread row, 3 CTAs per SM, tensor copies
-        if (fused_mt4_supported(a)) return launch_fused_mt4(a, fid, true, st, pdl);
+        if (fused_mt4_supported(a)) return launch_fused_mt4(a, fid, true, st);
         return fused_mt_supported(a) ? launch_fused_mt(a, fid, st) : launch_pa<8, 2, 8, 2, true>(a, fid, st);
       case 1: return launch_async<8, 2, 8, 2>(a, fid, st);      // async halos, one subdomain per cluster
       case 2: return launch_full<8, 4, 4, 1>(a, fid, st);       // cluster barrier per half-step: 512 threads

@@ -33,7 +33,6 @@
 
 #include "fused_common.cuh"
 #include "internal.cuh"
-#include "pdl.cuh"
 
 namespace ddtv {
 
@@ -228,13 +227,11 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
     if (l == 0) mbar_arrive_expect_tx(mbQ, kHaloBytes);
   };
 
-  griddep_wait();  // lambda comes from the multiplier update before; no state was touched yet
   if (first < T) prefetch(first);
   uint32_t nsub = 0;             // subdomains started (phase of mbL)
   int pa = -1, pc0 = 0, pgb = 0;  // previous subdomain, whose u and p1 wait in the out-buffer (TMA)
 
   for (int t = first; t < T; t += stride, ++nsub) {
-    if (t + stride >= T) griddep_launch();  // last subdomain: the next multiplier update may launch
     const int a = t / g.NC, b = t - a * g.NC;
     const int c0 = b * 128;
     const int gb = a * 128 + rank * BAND;
@@ -573,19 +570,17 @@ int mt4_grid(const LocalArgs& a, bool tma, int fid, bool mask) {
 }
 
 template <int FID, bool MASK>
-cudaError_t launch_mt4_one(const LocalArgs& a, bool pdl, cudaStream_t st) {
-  cudaLaunchAttribute attr[2];
+cudaError_t launch_mt4_one(const LocalArgs& a, cudaStream_t st) {
+  cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = mt4_config(mt4_grid(a, false, FID, MASK), false, attr);
-  if (pdl) allow_programmatic_launch(cfg, attr);
   cfg.stream = st;
   return cudaLaunchKernelEx(&cfg, k_fused_mt4<FID, MASK>, a);
 }
 
 template <int FID, bool MASK>
-cudaError_t launch_mt4t_one(const LocalArgs& a, const Mt4Maps& maps, bool pdl, cudaStream_t st) {
-  cudaLaunchAttribute attr[2];
+cudaError_t launch_mt4t_one(const LocalArgs& a, const Mt4Maps& maps, cudaStream_t st) {
+  cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = mt4_config(mt4_grid(a, true, FID, MASK), true, attr);
-  if (pdl) allow_programmatic_launch(cfg, attr);
   cfg.stream = st;
   return cudaLaunchKernelEx(&cfg, k_fused_mt4t<FID, MASK>, a, maps);
 }
@@ -648,22 +643,20 @@ cudaError_t fused_mt4_prepare() {
   return prepare_mt4_one<FID_SEG, false>();
 }
 
-cudaError_t launch_fused_mt4(const LocalArgs& a, int fid, bool tma, cudaStream_t st, bool pdl) {
+cudaError_t launch_fused_mt4(const LocalArgs& a, int fid, bool tma, cudaStream_t st) {
   const bool m = a.mask != nullptr;
   Mt4Maps maps;
   if (tma && encode_maps(a, &maps)) {
     switch (fid) {
-      case FID_L2:
-        return m ? launch_mt4t_one<FID_L2, true>(a, maps, pdl, st) : launch_mt4t_one<FID_L2, false>(a, maps, pdl, st);
-      case FID_L1:
-        return m ? launch_mt4t_one<FID_L1, true>(a, maps, pdl, st) : launch_mt4t_one<FID_L1, false>(a, maps, pdl, st);
-      default: return launch_mt4t_one<FID_SEG, false>(a, maps, pdl, st);
+      case FID_L2: return m ? launch_mt4t_one<FID_L2, true>(a, maps, st) : launch_mt4t_one<FID_L2, false>(a, maps, st);
+      case FID_L1: return m ? launch_mt4t_one<FID_L1, true>(a, maps, st) : launch_mt4t_one<FID_L1, false>(a, maps, st);
+      default: return launch_mt4t_one<FID_SEG, false>(a, maps, st);
     }
   }
   switch (fid) {
-    case FID_L2: return m ? launch_mt4_one<FID_L2, true>(a, pdl, st) : launch_mt4_one<FID_L2, false>(a, pdl, st);
-    case FID_L1: return m ? launch_mt4_one<FID_L1, true>(a, pdl, st) : launch_mt4_one<FID_L1, false>(a, pdl, st);
-    default: return launch_mt4_one<FID_SEG, false>(a, pdl, st);
+    case FID_L2: return m ? launch_mt4_one<FID_L2, true>(a, st) : launch_mt4_one<FID_L2, false>(a, st);
+    case FID_L1: return m ? launch_mt4_one<FID_L1, true>(a, st) : launch_mt4_one<FID_L1, false>(a, st);
+    default: return launch_mt4_one<FID_SEG, false>(a, st);
   }
 }
 

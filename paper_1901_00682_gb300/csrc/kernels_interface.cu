@@ -4,7 +4,6 @@
 // on compact interface strips, plus the kernels that move strips in and out of the
 // torn field.  The update is HBM-bound: 5 float reads and 1 write per interface edge.
 #include "internal.cuh"
-#include "pdl.cuh"
 
 namespace ddtv {
 
@@ -25,8 +24,6 @@ __global__ void k_interface_v4(int nh4, int nv4, float sigma, const float4* __re
                                const float4* __restrict__ cSR, const float4* __restrict__ cSL,
                                const float4* __restrict__ pSR, const float4* __restrict__ pSL,
                                float4* __restrict__ lamv) {
-  griddep_wait();    // the strips come from the local solves before
-  griddep_launch();  // the next local solves may start launching (they wait for lambda)
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nh4 + nv4; e += gridDim.x * blockDim.x) {
     const bool h = e < nh4;
     const int q = h ? e : e - nh4;
@@ -50,8 +47,6 @@ __global__ void k_interface_v1(int nh, int nv, float sigma, const float* __restr
                                const float* __restrict__ cSR, const float* __restrict__ cSL,
                                const float* __restrict__ pSR, const float* __restrict__ pSL,
                                float* __restrict__ lamv) {
-  griddep_wait();
-  griddep_launch();
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nh + nv; e += gridDim.x * blockDim.x) {
     if (e < nh) {
       lamh[e] = lam_step(lamh[e], sigma, cSB[e], pSB[e], cST[e], pST[e]);
@@ -140,26 +135,21 @@ int grid_for(long long n, int block) {
 }  // namespace
 
 cudaError_t launch_interface(const Grid& g, float sigma, Strips cur, Strips prev, float* lamh, float* lamv,
-                             cudaStream_t st, bool pdl) {
+                             cudaStream_t st) {
   const int nh = (g.NR - 1) * g.W, nv = (g.NC - 1) * g.H;
   if (nh + nv == 0) return cudaSuccess;
   const int block = 256;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  cfg.blockDim = dim3(block, 1, 1);
-  cfg.stream = st;
-  if (pdl) allow_programmatic_launch(cfg, attr);
   if (g.W % 4 == 0 && g.H % 4 == 0) {
     const int nh4 = nh / 4, nv4 = nv / 4;
-    cfg.gridDim = dim3(grid_for(nh4 + nv4, block), 1, 1);
-    return cudaLaunchKernelEx(&cfg, k_interface_v4, nh4, nv4, sigma, (const float4*)cur.SB, (const float4*)cur.ST,
-                              (const float4*)prev.SB, (const float4*)prev.ST, (float4*)lamh, (const float4*)cur.SR,
-                              (const float4*)cur.SL, (const float4*)prev.SR, (const float4*)prev.SL, (float4*)lamv);
+    k_interface_v4<<<grid_for(nh4 + nv4, block), block, 0, st>>>(
+        nh4, nv4, sigma, (const float4*)cur.SB, (const float4*)cur.ST, (const float4*)prev.SB,
+        (const float4*)prev.ST, (float4*)lamh, (const float4*)cur.SR, (const float4*)cur.SL, (const float4*)prev.SR,
+        (const float4*)prev.SL, (float4*)lamv);
+  } else {
+    k_interface_v1<<<grid_for(nh + nv, block), block, 0, st>>>(nh, nv, sigma, cur.SB, cur.ST, prev.SB, prev.ST,
+                                                                lamh, cur.SR, cur.SL, prev.SR, prev.SL, lamv);
   }
-  cfg.gridDim = dim3(grid_for(nh + nv, block), 1, 1);
-  return cudaLaunchKernelEx(&cfg, k_interface_v1, nh, nv, sigma, (const float*)cur.SB, (const float*)cur.ST,
-                            (const float*)prev.SB, (const float*)prev.ST, lamh, (const float*)cur.SR,
-                            (const float*)cur.SL, (const float*)prev.SR, (const float*)prev.SL, lamv);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_interface_batch(const BatchIfaceArgs& a, int total4, cudaStream_t st) {
