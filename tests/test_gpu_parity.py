@@ -80,6 +80,27 @@ def test_ragged_tiles_parity(H, W, NR, NC):
     _check(f, None, 30, sub_rows=NR, sub_cols=NC, fidelity="l2", alpha=10.0, inner_iters=7)
 
 
+@pytest.mark.parametrize("H,W,NR,NC", [(1, 1, 1, 1), (1, 2, 1, 2), (2, 1, 2, 1), (8, 8, 8, 8), (5, 7, 5, 7),
+                                       (1, 64, 1, 4), (64, 1, 4, 1)])
+def test_degenerate_geometries_parity(H, W, NR, NC):
+    """The method's degenerate cases: a single pixel (no dual dofs at all), single rows
+    and columns, and one-pixel subdomains (every dof of a subdomain is an interface
+    dof; the 1 x 2 image split into two pixels is the smallest decomposition).  Fused
+    and plain paths against the oracle, and against each other bit for bit."""
+    f = np.random.Generator(np.random.PCG64(1000 * H + W)).random((H, W)).astype(np.float32)
+    kw = dict(sub_rows=NR, sub_cols=NC, fidelity="l2", alpha=10.0, inner_iters=5)
+    n = 40
+    _, g, _, _ = _run_gpu(f, None, n, **kw)
+    _, gp, _, _ = _run_gpu(f, None, n, path="plain", **kw)
+    pr, o = _run_oracle(f, None, n, **kw)
+    assert np.abs(g["u"] - o.u).max() <= U_TOL
+    Jg = oracle.energy(pr, g["u"], f.astype(np.float64), None)
+    Jo = oracle.energy(pr, o.u, f.astype(np.float64), None)
+    assert abs(Jg - Jo) <= E_TOL * max(abs(Jo), 1.0), (Jg, Jo)   # J* = 0 for a single pixel
+    for k in ("u", "P1", "P2", "lamh", "lamv"):
+        assert np.array_equal(g[k], gp[k]), k
+
+
 def test_tvl1_inpainting_parity():
     f, mask, _ = synth.tvl1_inpaint_image(160, 96, 10, 0.1, 0.2, 2)
     _check(f, mask, 60, sub_rows=3, sub_cols=2, fidelity="l1", alpha=1.5, inner_iters=10)
