@@ -41,6 +41,7 @@ SEED = 0
 ENERGY_EVERY = 5
 METRIC = "Mpixel*iter/s at 4096^2 ROF"
 UNIT = "Mpixel*iter/s"
+ADAPT_CAP = 20  # inner iterations allowed per local solve under the adaptive stop
 WORKLOAD = "rof4096: ROF L2 denoising 4096x4096 fp32, alpha=8, 32x32 subdomains of 128x128, 10 inner/outer"
 SMEM_BYTES_PER_PX_ITER = 28  # minimum neighbour exchange per pixel per inner iteration
 JSTAR_FILE = os.path.join(ROOT, "tests", "golden", "jstar_rof4096_seed0.json")
@@ -407,6 +408,31 @@ def run_ours(args):
                 sp.close()
             if tta["fused"]["reached"] and tta["plain"]["reached"]:
                 tta["speedup_vs_plain"] = tta["plain"]["ms"] / tta["fused"]["ms"]
+            # adaptive inner stopping (eq. stop_inner1): the paper's tolerance and a loose
+            # one, at most ADAPT_CAP inner iterations per local solve
+            adaptive = {}
+            for itol in (1e-6, 1e-3):
+                key = f"inner_tol={itol:g}"
+                try:
+                    pt = L.make_params(H, W, NR, NC, fidelity="l2", alpha=ALPHA, inner_iters=ADAPT_CAP,
+                                       inner_tol=itol, outer_iters=3000, outer_tol=1e-4, energy_ref=rec["J_star"],
+                                       energy_every=ENERGY_EVERY)
+                    sp = L.Solver(pt, stream)
+                    u_out = torch.empty_like(fd)
+                    sp.solve_device(fd, None, u_out)  # warm-up run
+                    torch.cuda.synchronize(dev)
+                    t = time.perf_counter()
+                    _, stt, rc = sp.solve_device(fd, None, u_out)
+                    torch.cuda.synchronize(dev)
+                    dt = time.perf_counter() - t
+                    adaptive[key] = {"ms": dt * 1e3, "device_ms": stt.ms, "outer_iters": stt.outer_done,
+                                     "inner_cap": ADAPT_CAP, "max_inner_iters": stt.inner_max,
+                                     "mean_inner_iters": stt.pixel_iters / (H * W * max(stt.outer_done, 1)),
+                                     "rel_err": stt.rel_err, "reached": bool(stt.converged)}
+                    sp.close()
+                except L.DDTVError as e:
+                    adaptive[key] = {"error": str(e)}
+            tta["adaptive"] = adaptive
             if not args.no_tune:
                 from paper_1901_00682_gb300 import autotune
                 r = autotune.tune(fd, dict(fidelity="l2", alpha=ALPHA), tol=1e-4, j_ref=rec["J_star"],
