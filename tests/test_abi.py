@@ -100,3 +100,47 @@ def test_create_rejects_edge_counts_beyond_32_bit_numbering(lib):
     rc = lib.dd_tv_create(ctypes.byref(h), ctypes.byref(p))
     assert rc == _lib.EINVAL and not h.value
     assert "interface edges" in lib.dd_tv_last_error(None).decode()
+
+
+def _batch_args(**over):
+    from paper_1901_00682_gb300 import _lib
+    im = dict(height=256, width=128, fidelity=_lib.L2, alpha=10.0, c1=0.0, c2=0.0, tau=0.0, sigma=0.0)
+    pa = dict(tile=128, inner_iters=10, tau0=10.0, sigma0=1 / 80, variant=0)
+    for k, v in over.items():
+        (im if k in im else pa)[k] = v
+    arr = (_lib.BatchImage * 2)()
+    arr[0] = _lib.BatchImage(**im)
+    arr[1] = _lib.BatchImage(128, 128, _lib.SEG, 20.0, 0.2, 0.8, 1.0, 0.5)
+    return arr, _lib.BatchParams(**pa)
+
+
+@pytest.mark.parametrize("field,value,code,needle", [
+    ("height", 200, "EINVAL", "multiples of 128"),
+    ("width", 0, "EINVAL", "multiples of 128"),
+    ("fidelity", 9, "EINVAL", "fidelity"),
+    ("alpha", -2.0, "EINVAL", "alpha"),
+    ("alpha", math.inf, "EINVAL", "alpha"),
+    ("tau", 10.0, "EINVAL", "tau sigma"),          # tau given, sigma 0
+    ("tile", 64, "EUNSUPPORTED", "128"),
+    ("inner_iters", 0, "EINVAL", "inner_iters"),
+    ("sigma0", 0.1, "EINVAL", "tau0 sigma0"),
+    ("variant", 4, "EINVAL", "variant"),
+])
+def test_batch_create_rejects_invalid(lib, field, value, code, needle):
+    """The batched solver validates every image and the shared parameters on the host
+    and refuses bad ones before any device call."""
+    from paper_1901_00682_gb300 import _lib
+    arr, bp = _batch_args(**{field: value})
+    h = ctypes.c_void_p()
+    rc = lib.dd_tv_batch_create(ctypes.byref(h), arr, 2, ctypes.byref(bp))
+    assert rc == getattr(_lib, code) and not h.value
+    assert needle in lib.dd_tv_batch_last_error(None).decode()
+
+
+def test_batch_create_rejects_empty_batch(lib):
+    from paper_1901_00682_gb300 import _lib
+    arr, bp = _batch_args()
+    h = ctypes.c_void_p()
+    assert lib.dd_tv_batch_create(ctypes.byref(h), arr, 0, ctypes.byref(bp)) == _lib.EINVAL and not h.value
+    assert lib.dd_tv_batch_destroy(None) == _lib.OK
+    assert lib.dd_tv_batch_iterate(None, 1) == _lib.EINVAL
