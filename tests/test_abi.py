@@ -144,3 +144,27 @@ def test_batch_create_rejects_empty_batch(lib):
     assert lib.dd_tv_batch_create(ctypes.byref(h), arr, 0, ctypes.byref(bp)) == _lib.EINVAL and not h.value
     assert lib.dd_tv_batch_destroy(None) == _lib.OK
     assert lib.dd_tv_batch_iterate(None, 1) == _lib.EINVAL
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """No CPU fallback: loading a missing library raises ImportError."""
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_1901_00682_gb300 import _lib\n"
+            "try:\n    _lib.load(%r)\nexcept ImportError as e:\n    print('ImportError', e)\n") % (
+        ROOT, str(tmp_path / "libddtv.so"))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.startswith("ImportError"), r.stdout + r.stderr
+
+
+def test_product_code_never_touches_the_oracle():
+    """The library and its binding share nothing with the oracle: no module of the
+    package imports it, and no CUDA source includes or names its files."""
+    pkg = os.path.join(ROOT, "paper_1901_00682_gb300")
+    for path in glob.glob(os.path.join(pkg, "*.py")):
+        src = open(path).read()
+        assert not re.search(r"^\s*(import oracle|from oracle)", src, flags=re.M), path
+    for path in glob.glob(os.path.join(pkg, "csrc", "*")):
+        src = open(path).read()
+        assert "dd_tv_oracle" not in src and "oracle/" not in src, path
