@@ -48,12 +48,14 @@ struct SmemLayout {
 };
 
 // ADAPT: adaptive inner stopping (Section 5, eq. stop_inner1).  Every thread sums
-// (p^{k+1} - p^k)^2 and (p^{k+1})^2 over the tile dofs it owns (float32), the CTA adds
-// the threads' sums in float64 in a fixed order, every CTA stores its pair into every
-// cluster CTA's slot array through DSMEM, and after one more cluster barrier phase
-// every CTA adds the CL pairs in rank order: all CTAs of the tile take the same
-// decision.  The u-step's first cluster wait is then taken at the end of the
-// previous iteration's p-step instead.
+// (p^{k+1} - p^k)^2 and (p^{k+1})^2 over the tile dofs it owns, each warp adds its
+// threads' sums (float32, fixed shuffle order), one thread adds the warps' sums in
+// float64 in a fixed order and stores the CTA's pair into every cluster CTA's slot
+// array through DSMEM, and after one more cluster barrier phase one thread of every
+// CTA adds the CL pairs in rank order and shares the decision through shared memory:
+// all CTAs of the tile take the same decision.  (Float64 work stays with one thread:
+// the float64 pipe of this GPU is narrow.)  The u-step's first cluster wait is then
+// taken at the end of the previous iteration's p-step instead.
 template <int BW, int R, int TR, int CL, int FID, bool MASK, bool ADAPT>
 __global__ void __launch_bounds__(BW* TR, (BW * TR <= 256 ? 2 : 1)) k_fused(const LocalArgs A) {
   using L = SmemLayout<BW, R, TR>;
@@ -61,6 +63,7 @@ __global__ void __launch_bounds__(BW* TR, (BW * TR <= 256 ? 2 : 1)) k_fused(cons
   extern __shared__ float smem[];
   __shared__ double sRed[2 * CL];            // adaptive stop: per-rank (sum dp^2, sum p^2)
   __shared__ double sWarp[2 * (BW * TR / 32)];
+  __shared__ int sStop;                      // adaptive stop: the CTA's decision
   float* sU = smem + L::U;
   float* sUh = smem + L::UH;
   float* sQ2 = smem + L::Q2;
@@ -237,9 +240,10 @@ __global__ void __launch_bounds__(BW* TR, (BW * TR <= 256 ? 2 : 1)) k_fused(cons
     for (int r = 1; r < R; ++r) p_px(r, c);
     __syncthreads();
     if (ADAPT) {
-      // CTA sums: warps in order, then the warp partials in order (float64)
+      // warp sums in float32 (fixed shuffle order), then one thread adds the warps' sums in
+      // order in float64
       const int tid = ty * BW + j, lane = tid & 31, wid = tid >> 5;
-      double wd = sd, wp = sp;
+      float wd = sd, wp = sp;
       sd = sp = 0.f;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -274,12 +278,16 @@ __global__ void __launch_bounds__(BW* TR, (BW * TR <= 256 ? 2 : 1)) k_fused(cons
       } else {
         __syncthreads();
       }
-      double td = 0.0, tp = 0.0;
-      for (int q = 0; q < CL; ++q) {
-        td += sRed[2 * q];
-        tp += sRed[2 * q + 1];
+      if (tid == 0) {
+        double td = 0.0, tp = 0.0;
+        for (int q = 0; q < CL; ++q) {
+          td += sRed[2 * q];
+          tp += sRed[2 * q + 1];
+        }
+        sStop = (tp == 0.0 || td < A.inner_tol2 * tp) ? 1 : 0;
       }
-      if (tp == 0.0 || td < A.inner_tol2 * tp) {
+      __syncthreads();
+      if (sStop) {
         k_run = k + 1;
         break;
       }
