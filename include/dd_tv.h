@@ -81,9 +81,12 @@ typedef struct {
   double energy_ref;      /* J* used by outer_tol (eq. stop_outer)                           */
   int energy_every;       /* with outer_tol: evaluate J every energy_every outer iterations  */
   int path;               /* dd_tv_path                                                    */
-  int variant;            /* fused path: hardware mapping of a 128 x 128 subdomain (which
-                             CTA cluster shape and rows per thread), 0 = default; the
-                             arithmetic and results do not depend on it              */
+  int variant;            /* fused path, hardware mapping of exact 128 x 128 subdomains:
+                             0 persistent 4 x 4 micro-tiles, state moved by tensor
+                             copies (default); 1 the same with cp.async copies; 2
+                             persistent 2 x 4 micro-tiles; 3 one cluster per subdomain
+                             with cluster barriers (the kernel of every other tile
+                             shape).  The arithmetic and results do not depend on it  */
   double inner_tol;       /* >= 0.  0: every local solve runs inner_iters iterations.  > 0:
                              adaptive inner stopping (Section 5, eq. stop_inner1): a
                              subdomain stops after the first inner iteration k with
@@ -271,11 +274,8 @@ typedef struct {
   int tile;               /* subdomain side; 128 is the only value supported             */
   int inner_iters;        /* 1..DD_TV_MAX_INNER                                        */
   double tau0, sigma0;    /* initial inner steps (Section 5: 10 and 1/80)               */
-  int variant;            /* 0: persistent clusters over the batch's work list, 2 x 4
-                             pixel micro-tiles per thread (default); 1, 2: one cluster
-                             per subdomain, 256 / 512 threads; 3: persistent clusters,
-                             one pixel column per thread; the results do not depend
-                             on it                                                    */
+  int variant;            /* must be 0: persistent clusters over the batch's work list,
+                             2 x 4 pixel micro-tiles per thread                       */
 } dd_tv_batch_params;
 
 /* Validates and allocates the batch (images[n], n >= 1); *out = NULL on error. */

@@ -19,6 +19,7 @@ PATH_FUSED, PATH_PLAIN, PATH_FULLDIM = 0, 1, 2
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTCONV, EUNSUPPORTED = range(7)
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTCONV", 6: "EUNSUPPORTED"}
 MAX_INNER = 1024
+N_VARIANTS = 4  # hardware mappings of exact 128 x 128 subdomains (dd_tv_params.variant)
 
 
 class Params(ctypes.Structure):

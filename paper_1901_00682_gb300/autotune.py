@@ -206,7 +206,7 @@ if __name__ == "__main__":
     import torch
 
     import synth
-    vs = [int(x) for x in sys.argv[1].split(",")] if len(sys.argv) > 1 else list(range(16))
+    vs = [int(x) for x in sys.argv[1].split(",")] if len(sys.argv) > 1 else list(range(L.N_VARIANTS))
     img, _ = synth.rof_image(4096, 4096, 400, 0.1, 0)
     ms = time_variants(torch.from_numpy(img).cuda(), dict(fidelity="l2", alpha=8.0), 32, 32, vs)
     for v, t in ms.items():

@@ -150,7 +150,7 @@ int dd_tv_batch_create(dd_tv_batch** out, const dd_tv_batch_image* images, int n
   if (p->inner_iters < 1 || p->inner_iters > DD_TV_MAX_INNER) return bfail(nullptr, DD_TV_EINVAL, "bad inner_iters");
   if (!(p->tau0 > 0) || !(p->sigma0 > 0) || p->tau0 * p->sigma0 > 0.125 * (1 + 1e-12))
     return bfail(nullptr, DD_TV_EINVAL, "tau0, sigma0 must be > 0 with tau0 sigma0 <= 1/8");
-  if (p->variant < 0 || p->variant > 3) return bfail(nullptr, DD_TV_EINVAL, "batch variant must be in [0, 3]");
+  if (p->variant != 0) return bfail(nullptr, DD_TV_EINVAL, "batch variant must be 0");
   for (int i = 0; i < n; ++i) {
     const dd_tv_batch_image& m = images[i];
     if (m.height < 128 || m.width < 128 || m.height % 128 || m.width % 128)

@@ -188,18 +188,6 @@ __device__ __forceinline__ void cp_async16(float* dst_smem, const float* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-template <int R, int TR>
-struct PaLayout {
-  using F = FullLayout<R, TR>;
-  static constexpr int NT = 128 * TR;
-  static constexpr int ST = (F::FLOATS + 3) & ~3;          // staging [field][r][thread]: u, f, p1, p2
-  static constexpr int SX = ST + 4 * R * NT;               // extras [x][thread]
-  static constexpr int NX = 6 + R;                          // lamh above, P1 bottom, lamh below, lamv left[R], P2 right,
-                                                            // lamv right, initial pbar1 of the row below the band
-  static constexpr int MB = (SX + NX * NT + 1) & ~1;        // mbU, mbQ
-  static constexpr size_t BYTES = sizeof(float) * MB + 16;
-};
-
 // Source of the subdomains a persistent batch kernel iterates over: the number of
 // subdomains, their image's arguments and grid position, the strips that receive
 // their interface values, and a call of the tile body with the image's fidelity as a

@@ -114,12 +114,6 @@ int fused_num_variants();
 // Name of the configuration chosen for a tile shape and variant (for reports).
 const char* fused_config_name(int mr, int mc, int variant);
 
-// ---- kernels_fused_ghost.cu
-// Persistent fused local solver with one halo exchange per inner iteration (ghost row
-// above each CTA's band); 128 x 128 tiles only.
-cudaError_t launch_fused_pg(const LocalArgs& a, int fidelity, cudaStream_t st);
-cudaError_t fused_pg_prepare();
-
 // ---- kernels_fused_mt.cu
 // Persistent fused local solver on 2 x 4 micro-tiles (two columns by four rows per
 // thread); 128 x 128 tiles with u, f, P1 16-byte aligned (fused_mt_supported).
@@ -128,21 +122,6 @@ cudaError_t launch_fused_mt(const LocalArgs& a, int fidelity, cudaStream_t st);
 cudaError_t fused_mt_prepare();
 // The same kernel over the work list of a batch (every image's arrays 16-byte aligned).
 cudaError_t launch_fused_mt_batch(const BatchArgs& B, int total_tiles, cudaStream_t st);
-
-// ---- kernels_fused_wrow.cu
-// Persistent fused local solver with one warp per pair of rows (named-barrier
-// exchange between adjacent warps, bulk asynchronous copies of the state); 128 x 128
-// tiles with 16-byte aligned rows (fused_wrow_supported).
-bool fused_wrow_supported(const LocalArgs& a);
-cudaError_t launch_fused_wrow(const LocalArgs& a, int fidelity, cudaStream_t st);
-cudaError_t fused_wrow_prepare();
-
-// ---- kernels_fused_ps.cu
-// Persistent fused local solver, column mapping with 16-byte state copies and an
-// out-buffer; 128 x 128 tiles with 16-byte aligned rows (fused_ps_supported).
-bool fused_ps_supported(const LocalArgs& a);
-cudaError_t launch_fused_ps(const LocalArgs& a, int fidelity, cudaStream_t st);
-cudaError_t fused_ps_prepare();
 
 // ---- kernels_fused_mt4.cu
 // Persistent fused local solver on 4 x 4 micro-tiles, one warp per thread row, three

@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(BW* TR, MINB) k_adj_fused(const LocalArgs A, c
 
 // ---------------------------------------------------------------------------
 // The same reverse pass for subdomains of exactly 128 x 128 pixels, with the halo
-// exchange of the asynchronous forward kernel (k_fused_async): a halo row is stored
+// exchange of the persistent forward kernels (kernels_fused_mt.cu): a halo row is stored
 // into the neighbour CTA with st.async and counted on an mbarrier there; only the
 // warps that read a halo wait for it (bounded), and no cluster barrier runs inside the
 // loops.  The reverse iteration has the forward's pattern, so the two barriers go on

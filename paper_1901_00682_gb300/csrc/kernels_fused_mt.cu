@@ -1,9 +1,9 @@
 // Persistent fused local solver on 2 x 4 micro-tiles (128 x 128 subdomains).
 //
-// The persistent asynchronous kernel (kernels_fused.cu, fused_pa_body) gives each
-// thread one column of R rows: vertical neighbours sit in registers, but every pixel
-// trades its u and pbar2 with both neighbouring columns through shared memory in each
-// inner iteration, about 39 bytes of shared-memory traffic per pixel and iteration.
+// A mapping that gives each thread one column of R rows keeps vertical neighbours in
+// registers, but every pixel trades its u and pbar2 with both neighbouring columns
+// through shared memory in each inner iteration, about 39 bytes of shared-memory
+// traffic per pixel and iteration.
 // Here a thread owns a micro-tile of two adjacent columns and four rows.  Inside it
 // every neighbour is in registers, and the micro-tile exchanges only its edges, each
 // with one vector access per iteration:
@@ -24,11 +24,11 @@
 // a cluster of 8 CTAs covers a subdomain and loops over subdomains (persistent),
 // prefetching the next one with cp.async (16-byte copies for u, f and p1, whose rows
 // stay 16-byte aligned in the torn layout; 4-byte copies for p2).  Halo rows between
-// the CTAs of a cluster travel with st.async and mbarrier complete_tx as in
-// fused_pa_body (same phase protocol); every wait is bounded and a wait that runs out
+// the CTAs of a cluster travel with st.async and mbarrier complete_tx (one mbarrier
+// per halo direction, phases counted by both sides); every wait is bounded and a wait that runs out
 // sets the error flag.  The tile's right side (the p2 dofs of column 128) is updated
 // by lanes 0..3 of each thread row, its bottom side by the last thread row of the last
-// CTA, as in fused_pa_body.
+// CTA.
 #include "fused_common.cuh"
 #include "internal.cuh"
 

@@ -16,7 +16,7 @@
 // the lane to its left), and its warp's last-row u and first-row pbar1 with the warps
 // above and below; two CTA barriers order them.  Rows crossing CTAs travel with
 // st.async and mbarrier complete_tx (bounded waits, the same phase protocol as
-// fused_pa_body), and the next subdomain is prefetched with 16-byte cp.async copies
+// kernels_fused_mt.cu), and the next subdomain is prefetched with 16-byte cp.async copies
 // (p2 as a window starting on a 16-byte boundary: W + N_c must be a multiple of 4).
 // Rows are packed in pairs (r, r + 2) for the `*.f32x2` arithmetic; every value is
 // computed with the operations of the scalar iteration in the same order, so the

@@ -124,7 +124,7 @@ def _batch_args(**over):
     ("tile", 64, "EUNSUPPORTED", "128"),
     ("inner_iters", 0, "EINVAL", "inner_iters"),
     ("sigma0", 0.1, "EINVAL", "tau0 sigma0"),
-    ("variant", 4, "EINVAL", "variant"),
+    ("variant", 1, "EINVAL", "variant"),
 ])
 def test_batch_create_rejects_invalid(lib, field, value, code, needle):
     """The batched solver validates every image and the shared parameters on the host

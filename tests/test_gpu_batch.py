@@ -29,13 +29,12 @@ def _images():
     return out
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
-def test_batch_equals_single_image_solves_bitwise(variant):
-    """Every batch mapping (0: persistent clusters over the work list; 1, 2: one
-    cluster per subdomain) gives each image the bits of its own solve."""
+def test_batch_equals_single_image_solves_bitwise():
+    """The batch kernel (persistent clusters over the work list) gives each image the
+    bits of its own solve."""
     L = _lib()
     ims = _images()
-    b = L.Batch(ims, inner_iters=10, variant=variant)
+    b = L.Batch(ims, inner_iters=10)
     fs = [torch.from_numpy(m["f"]).cuda() for m in ims]
     b.load(fs)
     b.iterate(13)

@@ -280,7 +280,7 @@ def test_maximum_size_sampled_subdomains(side):
     torch.cuda.empty_cache()
 
 
-N_VARIANTS = 16  # hardware mappings of a 128 x 128 subdomain (dd_tv_params.variant)
+N_VARIANTS = 4  # hardware mappings of a 128 x 128 subdomain (dd_tv_params.variant)
 
 
 def test_variant_count():
@@ -294,13 +294,12 @@ def test_variant_count():
 
 @pytest.mark.parametrize("fid,mask_prob,K", [("l2", 0.2, 10), ("l1", 0.2, 10), ("seg", 0.0, 10), ("l2", 0.0, 70)])
 def test_persistent_variants_bitwise_all_fidelities(fid, mask_prob, K):
-    """The default 4 x 4 micro-tile mapping (tensor copies) against the column (11),
-    warp-row (12), 16-byte-copy (13), 2 x 4 micro-tile (14) and cp.async 4 x 4 (15)
-    mappings for every fidelity, with and without the inpainting mask, and with more
-    inner iterations than the kernels keep in shared memory (K = 70: coefficients 64..
-    come from global memory)."""
+    """The default 4 x 4 micro-tile mapping (tensor copies) against the cp.async 4 x 4
+    (1), 2 x 4 micro-tile (2) and cluster-barrier (3) mappings for every fidelity, with
+    and without the inpainting mask, and with more inner iterations than the kernels
+    keep in shared memory (K = 70: coefficients 64.. come from global memory)."""
     L = _gpu()
-    H, W = 384, 512  # 3 x 4 tiles: W + N_c = 516 keeps the p2 rows 16-byte aligned (variants 0, 12, 13)
+    H, W = 384, 512  # 3 x 4 tiles: W + N_c = 516 keeps the p2 rows 16-byte aligned (variants 0, 1)
     f, _ = synth.rof_image(H, W, 12, 0.1, 5)
     mask = None
     if mask_prob:
@@ -310,7 +309,7 @@ def test_persistent_variants_bitwise_all_fidelities(fid, mask_prob, K):
               inner_iters=K)
     if fid == "seg":
         kw.update(c1=0.2, c2=0.8, tau=1.0)
-    outs = [_run_gpu(f, mask, 5, variant=v, **kw)[1] for v in (0, 11, 12, 13, 14, 15)]
+    outs = [_run_gpu(f, mask, 5, variant=v, **kw)[1] for v in range(N_VARIANTS)]
     for o in outs[1:]:
         for k in ("u", "P1", "P2", "lamh", "lamv"):
             assert np.array_equal(outs[0][k], o[k]), k
@@ -321,7 +320,8 @@ def test_persistent_variants_bitwise_all_fidelities(fid, mask_prob, K):
 def test_fused_variants_bitwise_identical(H, W, NR, NC):
     """Every hardware mapping of a 128x128-class subdomain runs the same arithmetic.
     W + N_c a multiple of 4 (512 / 4 x 4, 1024 / 8 x 8) runs the mappings that copy p2
-    rows in 16-byte chunks; the other grids run their fallback (variant 11 or 14)."""
+    rows in 16-byte chunks; the other exact grids run the 2 x 4 mapping in their place,
+    and ragged grids the cluster-barrier kernel."""
     L = _gpu()
     f, _ = synth.rof_image(H, W, 12, 0.1, 12)
     outs = []
