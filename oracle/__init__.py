@@ -25,6 +25,7 @@ import ctypes
 import os
 import subprocess
 import threading
+from contextlib import contextmanager
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -40,16 +41,57 @@ L2, L1, SEG = 0, 1, 2
 _FID = {"l2": L2, "l1": L1, "seg": SEG, L2: L2, L1: L1, SEG: SEG}
 
 
+def _compile(src: str, out: str) -> None:
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+
+
 def build(force: bool = False) -> str:
     """Compiles the oracle with gcc (OpenMP, no FP contraction) into oracle/_build."""
     os.makedirs(_LIB_DIR, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11",
-               "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
+        _compile(_SRC, _LIB)
     return _LIB
+
+
+def source() -> str:
+    """The text of dd_tv_oracle.c."""
+    with open(_SRC) as fh:
+        return fh.read()
+
+
+def build_variant(text: str, out_dir: str) -> str:
+    """Compiles a modified copy of the oracle source (``text``) into ``out_dir`` and
+    returns the library path.  Used only by the tests that plant a mistake in a copy
+    of the oracle to show that a pin catches it."""
+    os.makedirs(out_dir, exist_ok=True)
+    src = os.path.join(out_dir, "dd_tv_oracle_variant.c")
+    with open(src, "w") as fh:
+        fh.write(text)
+    out = os.path.join(out_dir, "liboracle_variant.so")
+    _compile(src, out)
+    return out
+
+
+@contextmanager
+def using_library(path: str):
+    """Routes every call of this module to the oracle library at ``path`` (a build of
+    ``build_variant``) for the duration of the block."""
+    global _lib
+    main = _load()
+    lib = ctypes.CDLL(path)
+    for name, fn in _SIGNATURES.items():
+        g = getattr(lib, name)
+        g.restype, g.argtypes = fn
+    with _lock:
+        _lib = lib
+    try:
+        yield
+    finally:
+        with _lock:
+            _lib = main
 
 
 class _Params(ctypes.Structure):
@@ -66,32 +108,34 @@ _P = ctypes.POINTER(_Params)
 _I = ctypes.POINTER(ctypes.c_int)
 
 
+_i, _dd = ctypes.c_int, ctypes.c_double
+_SIGNATURES = {
+    "orc_prox": (None, [_i, _i, _D, _D, _U8, _dd, _dd, _dd, _D]),
+    "orc_div": (None, [_i, _i, _D, _D, _D]),
+    "orc_grad": (None, [_i, _i, _D, _D, _D]),
+    "orc_tv": (_dd, [_i, _i, _D]),
+    "orc_fidelity": (_dd, [_i, _i, _D, _D, _U8, _dd, _dd]),
+    "orc_energy": (_dd, [_P, _D, _D, _U8]),
+    "orc_dual_value": (_dd, [_P, _D, _D, _D, _U8]),
+    "orc_jump": (None, [_P, _D, _D, _D, _D]),
+    "orc_jump_adjoint": (None, [_P, _D, _D, _D, _D]),
+    "orc_tile_div": (None, [_i, _i, _D, _D, _D]),
+    "orc_tile_grad": (None, [_i, _i, _i, _i, _i, _i, _D, _D, _D]),
+    "orc_local_solve": (None, [_P, _i, _i, _i, _i, _i, _i, _D, _U8, _D, _D, _D, _D, _D, _i]),
+    "orc_dd_run": (_i, [_P, _D, _U8, _i, _D, _D, _D, _D, _D, _D, _D, _D]),
+    "orc_dd_run_ex": (_i, [_P, _D, _U8, _i, _dd, _I, _I, _D, _D, _D, _D, _D, _D, _D, _D, _D]),
+    "orc_cp_run": (_i, [_P, _D, _U8, _i, _D, _D, _D, _D, _D]),
+    "orc_rof_accel_run": (_i, [_P, _D, _i, _D, _D, _D, _D, _D]),
+    "orc_torn_to_global": (None, [_P, _D, _D, _D, _D]),
+}
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
             lib = ctypes.CDLL(build())
-            i, d, v = ctypes.c_int, ctypes.c_double, None
-            sig = {
-                "orc_prox": (v, [i, i, _D, _D, _U8, d, d, d, _D]),
-                "orc_div": (v, [i, i, _D, _D, _D]),
-                "orc_grad": (v, [i, i, _D, _D, _D]),
-                "orc_tv": (d, [i, i, _D]),
-                "orc_fidelity": (d, [i, i, _D, _D, _U8, d, d]),
-                "orc_energy": (d, [_P, _D, _D, _U8]),
-                "orc_dual_value": (d, [_P, _D, _D, _D, _U8]),
-                "orc_jump": (v, [_P, _D, _D, _D, _D]),
-                "orc_jump_adjoint": (v, [_P, _D, _D, _D, _D]),
-                "orc_tile_div": (v, [i, i, _D, _D, _D]),
-                "orc_tile_grad": (v, [i, i, i, i, i, i, _D, _D, _D]),
-                "orc_local_solve": (v, [_P, i, i, i, i, i, i, _D, _U8, _D, _D, _D, _D, _D, i]),
-                "orc_dd_run": (i, [_P, _D, _U8, i, _D, _D, _D, _D, _D, _D, _D, _D]),
-                "orc_dd_run_ex": (i, [_P, _D, _U8, i, d, _I, _I, _D, _D, _D, _D, _D, _D, _D, _D, _D]),
-                "orc_cp_run": (i, [_P, _D, _U8, i, _D, _D, _D, _D, _D]),
-                "orc_rof_accel_run": (i, [_P, _D, i, _D, _D, _D, _D, _D]),
-                "orc_torn_to_global": (v, [_P, _D, _D, _D, _D]),
-            }
-            for name, (res, args) in sig.items():
+            for name, (res, args) in _SIGNATURES.items():
                 fn = getattr(lib, name)
                 fn.restype = res
                 fn.argtypes = args

@@ -114,3 +114,75 @@ def l2_inpaint(f, alpha, mask):
     u = r.x[:n]
     J = 0.5 * alpha * np.sum((w * (u - fv)) ** 2) + np.abs(D @ u).sum()
     return u.reshape(H, W), J
+
+
+def tile_div_matrix(mr, mc, top=True, bottom=True, left=True, right=True):
+    """Dense div_s of one mr x mc tile (outflow: bottom - top + right - left, Section
+    2.3) on its dual dofs, written from the definition: columns are p1 ((mr+1) x mc,
+    edge k above row k) then p2 (mr x (mc+1), edge l left of column l), row-major.
+    Returns (D, active): D keeps only the columns of active dofs (a side on the image
+    boundary is not a dof); active is the boolean mask over all dofs."""
+    n1, n2 = (mr + 1) * mc, mr * (mc + 1)
+    D = np.zeros((mr * mc, n1 + n2))
+    for i in range(mr):
+        for j in range(mc):
+            q = i * mc + j
+            D[q, (i + 1) * mc + j] += 1.0
+            D[q, i * mc + j] -= 1.0
+            D[q, n1 + i * (mc + 1) + j + 1] += 1.0
+            D[q, n1 + i * (mc + 1) + j] -= 1.0
+    act = np.ones(n1 + n2, dtype=bool)
+    act[:mc] = top
+    act[mr * mc:n1] = bottom
+    act[n1::mc + 1] = left
+    act[n1 + mc::mc + 1] = right
+    return D[:, act], act
+
+
+def box_qp(Q, b, x0=None):
+    """argmin_{|x_i| <= 1} 1/2 x^T Q x + b^T x for a positive semidefinite Q: L-BFGS-B,
+    then the free variables solved exactly with the active set fixed.  Returns
+    (x, value, kkt) where kkt is the largest violation of the projected-gradient
+    optimality condition x = proj(x - grad)."""
+    n = len(b)
+    obj = lambda x: (0.5 * x @ Q @ x + b @ x, Q @ x + b)
+    kkt_of = lambda x: float(np.abs(x - np.clip(x - (Q @ x + b), -1, 1)).max())
+    x = np.zeros(n) if x0 is None else np.clip(x0, -1, 1)
+    best = (np.inf, x)
+    for _ in range(5):   # L-BFGS-B, then an exact solve on the free set; restart if needed
+        r = minimize(obj, x, jac=True, method="L-BFGS-B", bounds=[(-1, 1)] * n,
+                     options={"maxiter": 100000, "ftol": 1e-16, "gtol": 1e-14, "maxcor": 50})
+        x = r.x
+        for _ in range(10):
+            g = Q @ x + b
+            act = ((x <= -1 + 1e-9) & (g > 0)) | ((x >= 1 - 1e-9) & (g < 0))
+            y = np.where(act, np.sign(x), x)
+            fr = ~act
+            if fr.any():
+                sol, *_ = np.linalg.lstsq(Q[np.ix_(fr, fr)], -(b[fr] + Q[np.ix_(fr, act)] @ y[act]), rcond=None)
+                y[fr] = sol
+            x = np.clip(y, -1, 1)
+        k = kkt_of(x)
+        if k < best[0]:
+            best = (k, x)
+        if k < 1e-12:
+            break
+    k, x = best
+    return x, float(obj(x)[0]), k
+
+
+def rof_dual(f, alpha):
+    """A solution p of the ROF dual  min_{|p| <= 1} 1/(2 alpha) ||div p + alpha f||^2
+    (global field: p1 (H+1) x W, p2 H x (W+1), zero on the image boundary) and the
+    primal solution u = f + div p / alpha.  Returns (p1, p2, u, kkt)."""
+    H, W = f.shape
+    D = fd_matrix(H, W)          # D = -div^T on the interior edges
+    fv = f.ravel().astype(np.float64)
+    q, _, kkt = box_qp(D @ D.T / alpha, -(D @ fv))
+    u = fv - D.T @ q / alpha
+    nv = (H - 1) * W
+    p1 = np.zeros((H + 1, W))
+    p1[1:H] = q[:nv].reshape(H - 1, W)
+    p2 = np.zeros((H, W + 1))
+    p2[:, 1:W] = q[nv:].reshape(H, W - 1)
+    return p1, p2, u.reshape(H, W), kkt
