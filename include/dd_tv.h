@@ -249,6 +249,54 @@ int dd_tv_measure_smem_bandwidth(double* gbs_out);
 int dd_tv_energy_noalloc(const float* u_dev, const float* f_dev, const uint8_t* mask_dev, int height, int width,
                          int fidelity, double alpha, double c1, double c2, void* stream, double* J_out);
 
+/* ---- Row-block shards: one problem over several GPUs (one process per GPU).
+ * Algorithm 1 couples the subdomains only through the multiplier update on the
+ * interfaces (its first line: lambda^{n+1} = lambda^n + sigma B (2 p~^n - p~^{n-1})),
+ * so a contiguous block of tile rows can live on each GPU.  A shard handle owns tile
+ * rows [tile_row_begin, tile_row_end) of the problem p describes (the whole image's
+ * height, width and subdomain grid): its image is rows [row_begin, row_begin + rows)
+ * of f (dd_tv_shard_rows), which dd_tv_load takes as an ordinary rows x width device
+ * image.  The sides of its first and last tile rows that face another shard are
+ * interface sides ("cut"): their dual dofs are active, and the shard keeps its own
+ * copy of the multipliers on the cut lines.  Both shards beside a cut update those
+ * multipliers from the same four strips with the same float32 arithmetic, so the copies
+ * stay equal bit for bit; the only data that crosses is, per outer iteration, each
+ * shard's copy of p~^n on its cut sides (width floats per cut), and for the energy its
+ * first pixel row.  A run of S shards reproduces the single-handle run bit for bit.
+ *
+ * Per outer iteration: dd_tv_iterate(h, 1); dd_tv_shard_export into two width-float
+ * device buffers; send the top buffer to the shard above and the bottom one to the
+ * shard below (NCCL, or copies), receive theirs; dd_tv_shard_import.  The first outer
+ * iteration needs no exchange (p~^0 = p~^{-1} = 0).
+ *
+ * Requirements: the fused path, a fixed inner iteration count (inner_tol = 0), tile
+ * rows of equal height (height a multiple of sub_rows).  Errors: DD_TV_EINVAL for a
+ * bad range or uneven tile rows, DD_TV_EUNSUPPORTED for another path or inner_tol > 0.
+ * On a shard, dd_tv_iterate accepts one outer iteration per call, and dd_tv_solve,
+ * dd_tv_solve_device, dd_tv_get_state, dd_tv_set_state, dd_tv_gap and the adjoint
+ * calls return DD_TV_EUNSUPPORTED. */
+int dd_tv_create_shard(dd_tv** out, const dd_tv_params* p, int tile_row_begin, int tile_row_end);
+/* First image row and number of rows of the handle's image (0 and height for a whole
+ * image). */
+int dd_tv_shard_rows(const dd_tv* h, int* row_begin, int* rows);
+/* Copies the shard's own copies of p~^n (n = outer iterations run) on its cut sides:
+ * top_dev <- the normal components on its top side (width floats), bottom_dev <- those
+ * on its bottom side.  A buffer is required for each cut side and ignored otherwise.
+ * Asynchronous on the handle's stream. */
+int dd_tv_shard_export(dd_tv* h, float* top_dev, float* bottom_dev);
+/* Takes the neighbours' copies of p~^n on the same lines: above_dev from the shard
+ * above (its bottom side), below_dev from the shard below (its top side).  Call after
+ * dd_tv_iterate and before the next one.  Asynchronous on the handle's stream. */
+int dd_tv_shard_import(dd_tv* h, const float* above_dev, const float* below_dev);
+/* Copies the first and the last pixel row of the current u (width floats each; either
+ * pointer may be NULL).  Asynchronous. */
+int dd_tv_shard_edge_rows(dd_tv* h, float* first_row_dev, float* last_row_dev);
+/* The shard's part of J(u) = alpha F(u) + TV(u) (eq. model): alpha F and TV over its
+ * rows plus sum_j |u_below(0, j) - u(rows - 1, j)| across its bottom cut, row_below_dev
+ * being the first row of the shard below (required when the bottom side is cut).  The
+ * parts of all shards add up to J of the whole image.  Synchronous. */
+int dd_tv_shard_energy(dd_tv* h, const float* row_below_dev, double* J_out);
+
 /* ---- Batched solve (many images in one launch per phase).
  * Every image is an independent instance of the model problem (Section 3) solved by
  * Algorithm 1 with its own fidelity, alpha, c1, c2 and outer steps; all images share

@@ -86,6 +86,12 @@ SIGNATURES = {
     "dd_tv_adjoint_release": (_i, [_vp]),
     "dd_tv_set_alpha": (_i, [_vp, _d]),
     "dd_tv_fault_probe": (_i, [_vp, _i, _DP]),
+    "dd_tv_create_shard": (_i, [ctypes.POINTER(_vp), _PP, _i, _i]),
+    "dd_tv_shard_rows": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "dd_tv_shard_export": (_i, [_vp, _vp, _vp]),
+    "dd_tv_shard_import": (_i, [_vp, _vp, _vp]),
+    "dd_tv_shard_edge_rows": (_i, [_vp, _vp, _vp]),
+    "dd_tv_shard_energy": (_i, [_vp, _vp, _DP]),
 }
 
 _lock = threading.Lock()
@@ -174,12 +180,19 @@ class Solver:
     """Owns one dd_tv handle.  Device tensors are torch CUDA tensors (float32/uint8,
     contiguous); work runs on torch's current stream unless `stream` is given."""
 
-    def __init__(self, params: Params, stream=None):
+    def __init__(self, params: Params, stream=None, shard=None):
+        """shard = (tile_row_begin, tile_row_end): a row-block shard of the problem
+        `params` describes (dd_tv_create_shard); None: the whole image."""
         self.lib = load()
         self.params = params
         h = ctypes.c_void_p()
-        check(self.lib.dd_tv_create(ctypes.byref(h), ctypes.byref(params)), None)
+        if shard is None:
+            check(self.lib.dd_tv_create(ctypes.byref(h), ctypes.byref(params)), None)
+        else:
+            check(self.lib.dd_tv_create_shard(ctypes.byref(h), ctypes.byref(params), int(shard[0]),
+                                              int(shard[1])), None)
         self.h = h
+        self.shard = shard
         self.set_stream(stream)
 
     def set_stream(self, stream=None):
@@ -328,6 +341,27 @@ class Solver:
         ga = ctypes.c_double()
         check(self.lib.dd_tv_adjoint_backward(self.h, _ptr(grad_u), _ptr(grad_f_out), ctypes.byref(ga)), self.h)
         return ga.value
+
+    # -- row-block shards
+    def shard_rows(self):
+        """(first image row, rows) of the handle's image."""
+        r0, n = ctypes.c_int(), ctypes.c_int()
+        check(self.lib.dd_tv_shard_rows(self.h, ctypes.byref(r0), ctypes.byref(n)), self.h)
+        return r0.value, n.value
+
+    def shard_export(self, top, bottom):
+        check(self.lib.dd_tv_shard_export(self.h, _ptr(top), _ptr(bottom)), self.h)
+
+    def shard_import(self, above, below):
+        check(self.lib.dd_tv_shard_import(self.h, _ptr(above), _ptr(below)), self.h)
+
+    def shard_edge_rows(self, first, last):
+        check(self.lib.dd_tv_shard_edge_rows(self.h, _ptr(first), _ptr(last)), self.h)
+
+    def shard_energy(self, row_below) -> float:
+        J = ctypes.c_double()
+        check(self.lib.dd_tv_shard_energy(self.h, _ptr(row_below), ctypes.byref(J)), self.h)
+        return J.value
 
     def adjoint_release(self):
         check(self.lib.dd_tv_adjoint_release(self.h), self.h)

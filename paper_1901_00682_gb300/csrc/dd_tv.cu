@@ -65,7 +65,17 @@ struct dd_tv {
   float *f = nullptr, *u = nullptr, *P1 = nullptr, *P2 = nullptr, *lamh = nullptr, *lamv = nullptr;
   uint8_t* mask = nullptr;
   float* strip_mem = nullptr;
-  Strips strips[2] = {};
+  Strips strips[2] = {};   // every interface line of the handle (the multiplier update's view)
+  // The local solves' view of the horizontal lines: for a row-block shard whose top
+  // side is cut, line -1 (the cut above) precedes line 0 in memory, so these point one
+  // line into the arrays above; for a whole image they equal lamh / strips.
+  float* lamh_k = nullptr;
+  Strips strips_k[2] = {};
+  // row-block shard (dd_tv_create_shard): global tile rows [tile_row0, tile_row0 + g.NR)
+  // of a problem with nr_global tile rows; its first pixel row is row0 of the image
+  bool shard = false;
+  int tile_row0 = 0, nr_global = 0, row0 = 0;
+  size_t nlh = 0;          // horizontal interface lines held, cut lines included
   Coef* coef = nullptr;
   // plain path: phat and pbar; full-dimension path: pbar (carried across iterations)
   float *Ph1 = nullptr, *Ph2 = nullptr, *Pb1 = nullptr, *Pb2 = nullptr;
@@ -103,6 +113,13 @@ int fail(dd_tv* h, int code, const char* fmt, ...) {
     va_end(ap);
   }
   return code;
+}
+
+// a shard exchanges its cut strips with its neighbours between outer iterations, so
+// the calls that run several outer iterations or read the global state refuse it
+int refuse_shard(dd_tv* h, const char* what) {
+  return fail(h, DD_TV_EUNSUPPORTED, "%s is not available on a shard (one outer iteration per dd_tv_iterate call, "
+              "with dd_tv_shard_export / dd_tv_shard_import between calls)", what);
 }
 
 #define CK(call)                                                                                  \
@@ -208,9 +225,9 @@ LocalArgs local_args(dd_tv* h, int write_set) {
   a.u = h->u;
   a.P1 = h->P1;
   a.P2 = h->P2;
-  a.lamh = h->lamh;
+  a.lamh = h->lamh_k;
   a.lamv = h->lamv;
-  a.out = h->strips[write_set];
+  a.out = h->strips_k[write_set];
   a.coef = h->coef;
   a.err = h->flag;
   a.inner_tol2 = h->p.inner_tol * h->p.inner_tol;
@@ -259,7 +276,11 @@ cudaError_t outer_once(dd_tv* h, int par) {
   }
   {
     PhaseMark m(h, 0, (h->nh + h->nv) ? 1 : 0);
-    if ((e = launch_interface(h->g, (float)h->p.sigma, h->strips[par], h->strips[1 - par], h->lamh, h->lamv, st)) !=
+    // the multiplier update runs over every line the handle holds (a shard's cut lines
+    // included): a grid with nlh + 1 tile rows has nlh horizontal interface lines
+    Grid gi = h->g;
+    gi.NR = (int)h->nlh + 1;
+    if ((e = launch_interface(gi, (float)h->p.sigma, h->strips[par], h->strips[1 - par], h->lamh, h->lamv, st)) !=
         cudaSuccess)
       return e;
   }
@@ -720,12 +741,31 @@ void dd_tv_default_params(dd_tv_params* p) {
   p->inner_tol = 0.0;
 }
 
-int dd_tv_create(dd_tv** out, const dd_tv_params* p) {
+namespace {
+
+// a0 < 0: the whole image; otherwise the row-block shard of tile rows [a0, a1)
+int create_impl(dd_tv** out, const dd_tv_params* p, int a0, int a1) {
   if (!out) return DD_TV_EINVAL;
   *out = nullptr;
   dd_tv* h = new (std::nothrow) dd_tv();
   if (!h) return DD_TV_ENOMEM;
   int rc = validate(p, h->err, sizeof(h->err));
+  if (!rc && a0 >= 0) {
+    if (p->path != DD_TV_PATH_FUSED) {
+      fail(h, DD_TV_EUNSUPPORTED, "a shard runs the fused path only");
+      rc = DD_TV_EUNSUPPORTED;
+    } else if (p->inner_tol > 0.0) {
+      fail(h, DD_TV_EUNSUPPORTED, "a shard runs a fixed number of inner iterations (inner_tol must be 0)");
+      rc = DD_TV_EUNSUPPORTED;
+    } else if (a1 <= a0 || a1 > p->sub_rows) {
+      fail(h, DD_TV_EINVAL, "shard tile rows [%d, %d) must be a nonempty range inside [0, %d)", a0, a1, p->sub_rows);
+      rc = DD_TV_EINVAL;
+    } else if (p->height % p->sub_rows != 0) {
+      fail(h, DD_TV_EINVAL, "sharding needs tile rows of equal height: height %d is not a multiple of sub_rows %d",
+           p->height, p->sub_rows);
+      rc = DD_TV_EINVAL;
+    }
+  }
   if (rc) {
     std::snprintf(g_create_err, sizeof(g_create_err), "%s", h->err);
     delete h;
@@ -735,6 +775,19 @@ int dd_tv_create(dd_tv** out, const dd_tv_params* p) {
   h->fid = p->fidelity;
   const bool full = p->path == DD_TV_PATH_FULLDIM;
   h->g = Grid{p->height, p->width, full ? 1 : p->sub_rows, full ? 1 : p->sub_cols};
+  if (a0 >= 0) {
+    // the shard's own problem: its rows, with the sides towards other shards cut
+    const int th = p->height / p->sub_rows;
+    h->shard = true;
+    h->tile_row0 = a0;
+    h->nr_global = p->sub_rows;
+    h->row0 = a0 * th;
+    h->g = Grid{(a1 - a0) * th, p->width, a1 - a0, p->sub_cols};
+    h->g.cut_top = a0 > 0;
+    h->g.cut_bot = a1 < p->sub_rows;
+    h->p.height = h->g.H;
+    h->p.sub_rows = h->g.NR;
+  }
   if (p->inner_tol > 0.0 && p->path != DD_TV_PATH_FUSED) {
     fail(h, DD_TV_EUNSUPPORTED, "inner_tol > 0 (adaptive inner stopping) needs the fused path");
     std::snprintf(g_create_err, sizeof(g_create_err), "%s", h->err);
@@ -765,7 +818,8 @@ int dd_tv_create(dd_tv** out, const dd_tv_params* p) {
   h->npx = (size_t)g.H * g.W;
   h->n1 = (size_t)(g.H + g.NR) * g.W;
   h->n2 = (size_t)g.H * (g.W + g.NC);
-  h->nh = (size_t)(g.NR - 1) * g.W;
+  h->nlh = (size_t)(g.NR - 1) + g.cut_top + g.cut_bot;
+  h->nh = h->nlh * g.W;
   h->nv = (size_t)(g.NC - 1) * g.H;
   std::vector<Coef> sched;
   build_schedule(*p, sched);
@@ -800,7 +854,14 @@ int dd_tv_create(dd_tv** out, const dd_tv_params* p) {
     h->strips[s].ST = base ? base + h->nh : nullptr;
     h->strips[s].SR = base ? base + 2 * h->nh : nullptr;
     h->strips[s].SL = base ? base + 2 * h->nh + h->nv : nullptr;
+    const size_t skip = (size_t)g.cut_top * g.W;  // the cut line above comes first
+    h->strips_k[s] = h->strips[s];
+    if (base) {
+      h->strips_k[s].SB += skip;
+      h->strips_k[s].ST += skip;
+    }
   }
+  h->lamh_k = h->lamh ? h->lamh + (size_t)g.cut_top * g.W : nullptr;
   cudaError_t e;
   if ((e = cudaMemcpy(h->coef, sched.data(), sched.size() * sizeof(Coef), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemset(h->counter, 0, sizeof(unsigned int))) != cudaSuccess ||
@@ -814,6 +875,20 @@ int dd_tv_create(dd_tv** out, const dd_tv_params* p) {
   h->stream = h->own;
   *out = h;
   return DD_TV_OK;
+}
+
+}  // namespace
+
+int dd_tv_create(dd_tv** out, const dd_tv_params* p) { return create_impl(out, p, -1, -1); }
+
+int dd_tv_create_shard(dd_tv** out, const dd_tv_params* p, int tile_row_begin, int tile_row_end) {
+  if (tile_row_begin < 0) {
+    if (out) *out = nullptr;
+    std::snprintf(g_create_err, sizeof(g_create_err), "shard tile rows must start at 0 or later (got %d)",
+                  tile_row_begin);
+    return DD_TV_EINVAL;
+  }
+  return create_impl(out, p, tile_row_begin, tile_row_end);
 }
 
 int dd_tv_destroy(dd_tv* h) {
@@ -856,6 +931,7 @@ int dd_tv_iterate(dd_tv* h, int n_outer) {
   if (!h) return DD_TV_EINVAL;
   if (!h->loaded) return fail(h, DD_TV_EINVAL, "no data loaded (dd_tv_load or dd_tv_set_state first)");
   if (n_outer < 0) return fail(h, DD_TV_EINVAL, "n_outer must be >= 0");
+  if (h->shard && n_outer > 1) return fail(h, DD_TV_EINVAL, "a shard runs one outer iteration per call (got %d)", n_outer);
   return run_outer(h, n_outer);
 }
 
@@ -889,6 +965,7 @@ int dd_tv_get_u(dd_tv* h, float* u_dev) {
 
 int dd_tv_solve(dd_tv* h, const float* f_host, const uint8_t* mask_host, float* u_host, dd_tv_stats* stats) {
   if (!h) return DD_TV_EINVAL;
+  if (h->shard) return refuse_shard(h, "dd_tv_solve");
   if (!u_host) return fail(h, DD_TV_EINVAL, "u is NULL");
   int rc = load_common(h, f_host, mask_host, cudaMemcpyHostToDevice);
   if (rc) return rc;
@@ -901,6 +978,7 @@ int dd_tv_solve(dd_tv* h, const float* f_host, const uint8_t* mask_host, float* 
 
 int dd_tv_solve_device(dd_tv* h, const float* f_dev, const uint8_t* mask_dev, float* u_dev, dd_tv_stats* stats) {
   if (!h) return DD_TV_EINVAL;
+  if (h->shard) return refuse_shard(h, "dd_tv_solve_device");
   if (!u_dev) return fail(h, DD_TV_EINVAL, "u is NULL");
   int rc = load_common(h, f_dev, mask_dev, cudaMemcpyDeviceToDevice);
   if (rc) return rc;
@@ -913,6 +991,7 @@ int dd_tv_solve_device(dd_tv* h, const float* f_dev, const uint8_t* mask_dev, fl
 int dd_tv_get_state(dd_tv* h, float* u, float* P1, float* P2, float* lamh, float* lamv, float* P1prev,
                     float* P2prev) {
   if (!h) return DD_TV_EINVAL;
+  if (h->shard) return refuse_shard(h, "dd_tv_get_state");
   const cudaStream_t st = h->stream;
   const auto D2D = cudaMemcpyDeviceToDevice;
   if (u) CK(cudaMemcpyAsync(u, h->u, h->npx * sizeof(float), D2D, st));
@@ -936,6 +1015,7 @@ int dd_tv_get_state(dd_tv* h, float* u, float* P1, float* P2, float* lamh, float
 int dd_tv_set_state(dd_tv* h, const float* u, const float* P1, const float* P2, const float* lamh,
                     const float* lamv, const float* P1prev, const float* P2prev, int outer_count) {
   if (!h) return DD_TV_EINVAL;
+  if (h->shard) return refuse_shard(h, "dd_tv_set_state");
   if (!u || !P1 || !P2) return fail(h, DD_TV_EINVAL, "u, P1 and P2 are required");
   if ((h->nh && !lamh) || (h->nv && !lamv)) return fail(h, DD_TV_EINVAL, "multipliers are required");
   if (!P1prev || !P2prev) return fail(h, DD_TV_EINVAL, "P1prev and P2prev are required");
@@ -971,6 +1051,7 @@ int dd_tv_energy(dd_tv* h, const float* u_dev, const float* f_dev, const uint8_t
 
 int dd_tv_gap(dd_tv* h, double* J_out, double* D_out) {
   if (!h) return DD_TV_EINVAL;
+  if (h->shard) return refuse_shard(h, "dd_tv_gap");
   if (!h->loaded) return fail(h, DD_TV_EINVAL, "no data loaded");
   const bool dual = h->fid == DD_TV_SEG || (h->fid == DD_TV_L2 && !h->has_mask);
   double o[2];
@@ -1017,6 +1098,7 @@ int dd_tv_set_alpha(dd_tv* h, double alpha) {
 int dd_tv_adjoint_forward(dd_tv* h, const float* f_dev, const uint8_t* mask_dev, int n_outer, int checkpoint_every,
                           float* u_dev) {
   if (!h) return DD_TV_EINVAL;
+  if (h->shard) return refuse_shard(h, "dd_tv_adjoint_forward");
   if (h->p.path == DD_TV_PATH_FULLDIM)
     return fail(h, DD_TV_EUNSUPPORTED, "the adjoint is defined for the decomposed paths only");
   if (!u_dev) return fail(h, DD_TV_EINVAL, "u is NULL");
@@ -1045,6 +1127,7 @@ int dd_tv_adjoint_forward(dd_tv* h, const float* f_dev, const uint8_t* mask_dev,
 
 int dd_tv_adjoint_backward(dd_tv* h, const float* grad_u_dev, float* grad_f_dev, double* grad_alpha) {
   if (!h) return DD_TV_EINVAL;
+  if (h->shard) return refuse_shard(h, "dd_tv_adjoint_backward");
   if (!grad_u_dev || !grad_f_dev || !grad_alpha) return fail(h, DD_TV_EINVAL, "grad_u, grad_f and grad_alpha are required");
   AdjointWork* w = h->adj;
   if (!w || w->gen != h->gen) return fail(h, DD_TV_EINVAL, "no dd_tv_adjoint_forward since the last load");
@@ -1142,3 +1225,73 @@ int dd_tv_fault_probe(dd_tv* h, int kind, double* waited_ms) {
 }
 
 }  // extern "C"
+
+// ---- row-block shards (dd_tv_create_shard)
+
+int dd_tv_shard_rows(const dd_tv* h, int* row_begin, int* rows) {
+  if (!h) return DD_TV_EINVAL;
+  if (row_begin) *row_begin = h->shard ? h->row0 : 0;
+  if (rows) *rows = h->g.H;
+  return DD_TV_OK;
+}
+
+int dd_tv_shard_export(dd_tv* h, float* top_dev, float* bottom_dev) {
+  if (!h) return DD_TV_EINVAL;
+  if (!h->shard) return fail(h, DD_TV_EINVAL, "not a shard");
+  const Grid& g = h->g;
+  if ((g.cut_top && !top_dev) || (g.cut_bot && !bottom_dev))
+    return fail(h, DD_TV_EINVAL, "a buffer is required for every cut side (top %d, bottom %d)", g.cut_top, g.cut_bot);
+  // this shard's copies on its cut sides of p~^n, n = outer iterations run: the t-side
+  // copy of the line above (its top side) and the s-side copy of the line below
+  const Strips& s = h->strips[h->n & 1];
+  const size_t W = (size_t)g.W;
+  if (g.cut_top) CK(cudaMemcpyAsync(top_dev, s.ST, W * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  if (g.cut_bot)
+    CK(cudaMemcpyAsync(bottom_dev, s.SB + (h->nlh - 1) * W, W * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  return DD_TV_OK;
+}
+
+int dd_tv_shard_import(dd_tv* h, const float* above_dev, const float* below_dev) {
+  if (!h) return DD_TV_EINVAL;
+  if (!h->shard) return fail(h, DD_TV_EINVAL, "not a shard");
+  const Grid& g = h->g;
+  if ((g.cut_top && !above_dev) || (g.cut_bot && !below_dev))
+    return fail(h, DD_TV_EINVAL, "a buffer is required for every cut side (top %d, bottom %d)", g.cut_top, g.cut_bot);
+  // the neighbours' copies of the same p~^n: the s-side copy of the line above (the
+  // bottom side of the shard above) and the t-side copy of the line below
+  const Strips& s = h->strips[h->n & 1];
+  const size_t W = (size_t)g.W;
+  if (g.cut_top) CK(cudaMemcpyAsync(s.SB, above_dev, W * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  if (g.cut_bot)
+    CK(cudaMemcpyAsync(s.ST + (h->nlh - 1) * W, below_dev, W * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  return DD_TV_OK;
+}
+
+int dd_tv_shard_edge_rows(dd_tv* h, float* first_row_dev, float* last_row_dev) {
+  if (!h) return DD_TV_EINVAL;
+  if (!h->loaded) return fail(h, DD_TV_EINVAL, "no data loaded");
+  const size_t W = (size_t)h->g.W;
+  if (first_row_dev) CK(cudaMemcpyAsync(first_row_dev, h->u, W * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  if (last_row_dev)
+    CK(cudaMemcpyAsync(last_row_dev, h->u + (size_t)(h->g.H - 1) * W, W * sizeof(float), cudaMemcpyDeviceToDevice,
+                       h->stream));
+  return DD_TV_OK;
+}
+
+int dd_tv_shard_energy(dd_tv* h, const float* row_below_dev, double* J_out) {
+  if (!h) return DD_TV_EINVAL;
+  if (!h->loaded) return fail(h, DD_TV_EINVAL, "no data loaded");
+  if (!J_out) return fail(h, DD_TV_EINVAL, "J_out is NULL");
+  if (h->g.cut_bot && !row_below_dev) return fail(h, DD_TV_EINVAL, "the bottom side is cut: row_below is required");
+  double o[2];
+  int rc = energy_of(h, h->u, h->f, h->has_mask ? h->mask : nullptr, false, o);
+  if (rc) return rc;
+  double cut = 0.0;
+  if (h->g.cut_bot) {
+    CK(launch_row_tv(row_below_dev, h->u + (size_t)(h->g.H - 1) * h->g.W, h->g.W, h->red_out + 1, h->stream));
+    CK(cudaMemcpyAsync(&cut, h->red_out + 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  *J_out = o[0] + cut;
+  return DD_TV_OK;
+}

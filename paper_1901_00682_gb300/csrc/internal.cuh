@@ -9,9 +9,14 @@
 
 namespace ddtv {
 
-// Image and subdomain grid.
+// Image and subdomain grid.  cut_top / cut_bot: the top side of tile row 0 / the
+// bottom side of tile row NR-1 lies on an interface with a neighbouring row-block
+// shard (its dofs are active, its multipliers and strips sit one line before / after
+// the handle's own lines); 0 for a whole image, where those sides are on the image
+// boundary.
 struct Grid {
   int H, W, NR, NC;
+  int cut_top = 0, cut_bot = 0;
 };
 
 // Interface strips: the interface values of one torn dual field p~^n.
@@ -153,6 +158,8 @@ cudaError_t launch_energy(const Grid& g, int fidelity, float alpha, float c1, fl
                           const float* f, const uint8_t* mask, const float* P1, const float* P2, double* partials,
                           unsigned int* counter, double* out, cudaStream_t st);
 int reduce_partials_count();
+// out[0] = sum_j |a_j - b_j|, j < n (float64, deterministic)
+cudaError_t launch_row_tv(const float* a, const float* b, int n, double* out, cudaStream_t st);
 
 // ---- kernels_adjoint.cu
 // u-step / p-step of the plain path that also record ubar (H x W) and the projection's

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(BW* TR, (BW * TR <= 256 ? 2 : 1)) k_fused(cons
   const int b = blockIdx.y, a = blockIdx.z;
   const int r0 = part_start(a, g.H, g.NR), mr = part_start(a + 1, g.H, g.NR) - r0;
   const int c0 = part_start(b, g.W, g.NC), mc = part_start(b + 1, g.W, g.NC) - c0;
-  const bool s_top = a > 0, s_bot = a + 1 < g.NR, s_lft = b > 0, s_rgt = b + 1 < g.NC;
+  const bool s_top = a > 0 || g.cut_top, s_bot = a + 1 < g.NR || g.cut_bot, s_lft = b > 0, s_rgt = b + 1 < g.NC;
   const int j = threadIdx.x, ty = threadIdx.y;
   const int lr0 = ty * R;            // first band row of this thread
   const int i0 = rank * BAND + lr0;  // first tile row of this thread
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(BW* TR, (BW * TR <= 256 ? 2 : 1)) k_fused(cons
       if (MASK && A.mask[px]) in_d |= 1u << r;
       a1 = A.P1[(size_t)(gi + a) * g.W + gj];
       a2 = A.P2[(size_t)gi * W2 + gj + b];
-      b1 = (i == 0 && s_top) ? phat_t(a1, A.lamh[(size_t)(a - 1) * g.W + gj], tau) : a1;
+      b1 = (i == 0 && s_top) ? phat_t(a1, A.lamh[(ptrdiff_t)(a - 1) * g.W + gj], tau) : a1;
       b2 = (j == 0 && s_lft) ? phat_t(a2, A.lamv[(size_t)(b - 1) * g.H + gi], tau) : a2;
       if (i == mr - 1 && s_bot) {
         pB = A.P1[(size_t)(gi + a + 1) * g.W + gj];
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(BW* TR, (BW * TR <= 256 ? 2 : 1)) k_fused(cons
       A.u[(size_t)gi * g.W + gj] = u[r];
       A.P1[(size_t)(gi + a) * g.W + gj] = p1[r];
       A.P2[(size_t)gi * W2 + gj + b] = p2[r];
-      if (i == 0 && s_top) A.out.ST[(size_t)(a - 1) * g.W + gj] = p1[r];
+      if (i == 0 && s_top) A.out.ST[(ptrdiff_t)(a - 1) * g.W + gj] = p1[r];
       if (j == 0 && s_lft) A.out.SL[(size_t)(b - 1) * g.H + gi] = p2[r];
       if (i == mr - 1 && s_bot) {
         A.P1[(size_t)(gi + a + 1) * g.W + gj] = pB;

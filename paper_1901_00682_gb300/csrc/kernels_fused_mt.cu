@@ -162,11 +162,11 @@ __device__ __forceinline__ void fused_mt_body(const LocalArgs& A, const int firs
         }
       }
     }
-    if (i0 == 0 && a > 0) {
-      cp_async4(smem + L::XLT + j0, A.lamh + (size_t)(a - 1) * g.W + c0 + j0);
-      cp_async4(smem + L::XLT + j0 + 1, A.lamh + (size_t)(a - 1) * g.W + c0 + j0 + 1);
+    if (i0 == 0 && (a > 0 || g.cut_top)) {
+      cp_async4(smem + L::XLT + j0, A.lamh + (ptrdiff_t)(a - 1) * g.W + c0 + j0);
+      cp_async4(smem + L::XLT + j0 + 1, A.lamh + (ptrdiff_t)(a - 1) * g.W + c0 + j0 + 1);
     }
-    if (last_row_here && a + 1 < g.NR) {
+    if (last_row_here && (a + 1 < g.NR || g.cut_bot)) {
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         cp_async4(smem + L::XPB + j0 + c, A.P1 + (size_t)(a * 128 + 128 + a) * g.W + c0 + j0 + c);
@@ -204,7 +204,7 @@ __device__ __forceinline__ void fused_mt_body(const LocalArgs& A, const int firs
     const int a = t / g.NC, b = t - a * g.NC;
     const int c0 = b * 128;
     const int gb = a * 128 + rank * BAND;
-    const bool s_top = a > 0, s_bot = a + 1 < g.NR, s_lft = b > 0, s_rgt = b + 1 < g.NC;
+    const bool s_top = a > 0 || g.cut_top, s_bot = a + 1 < g.NR || g.cut_bot, s_lft = b > 0, s_rgt = b + 1 < g.NC;
     const float lim_left = (tx == 0 && !s_lft) ? 0.f : 1.f;
     const float lim_top = (i0 == 0 && !s_top) ? 0.f : 1.f;
     const bool right_lane = s_rgt && tx < 4;
@@ -408,8 +408,8 @@ __device__ __forceinline__ void fused_mt_body(const LocalArgs& A, const int firs
       p2row[1] = lane_of(P2[1][e], h);
     }
     if (i0 == 0 && s_top) {
-      A.out.ST[(size_t)(a - 1) * g.W + c0 + j0] = lo2(P1[0][0]);
-      A.out.ST[(size_t)(a - 1) * g.W + c0 + j0 + 1] = lo2(P1[1][0]);
+      A.out.ST[(ptrdiff_t)(a - 1) * g.W + c0 + j0] = lo2(P1[0][0]);
+      A.out.ST[(ptrdiff_t)(a - 1) * g.W + c0 + j0 + 1] = lo2(P1[1][0]);
     }
     if (tx == 0 && s_lft) {
 #pragma unroll
@@ -528,11 +528,11 @@ __device__ __forceinline__ void fused_mt_run(const Src& S, const int first, cons
         }
       }
     }
-    if (i0 == 0 && a > 0) {
-      cp_async4(smem + L::XLT + j0, A.lamh + (size_t)(a - 1) * g.W + c0 + j0);
-      cp_async4(smem + L::XLT + j0 + 1, A.lamh + (size_t)(a - 1) * g.W + c0 + j0 + 1);
+    if (i0 == 0 && (a > 0 || g.cut_top)) {
+      cp_async4(smem + L::XLT + j0, A.lamh + (ptrdiff_t)(a - 1) * g.W + c0 + j0);
+      cp_async4(smem + L::XLT + j0 + 1, A.lamh + (ptrdiff_t)(a - 1) * g.W + c0 + j0 + 1);
     }
-    if (last_row_here && a + 1 < g.NR) {
+    if (last_row_here && (a + 1 < g.NR || g.cut_bot)) {
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         cp_async4(smem + L::XPB + j0 + c, A.P1 + (size_t)(a * 128 + 128 + a) * g.W + c0 + j0 + c);
@@ -576,7 +576,7 @@ __device__ __forceinline__ void fused_mt_run(const Src& S, const int first, cons
     const int a = lt / g.NC, b = lt - a * g.NC;
     const int c0 = b * 128;
     const int gb = a * 128 + rank * BAND;
-    const bool s_top = a > 0, s_bot = a + 1 < g.NR, s_lft = b > 0, s_rgt = b + 1 < g.NC;
+    const bool s_top = a > 0 || g.cut_top, s_bot = a + 1 < g.NR || g.cut_bot, s_lft = b > 0, s_rgt = b + 1 < g.NC;
     const float lim_left = (tx == 0 && !s_lft) ? 0.f : 1.f;
     const float lim_top = (i0 == 0 && !s_top) ? 0.f : 1.f;
     const bool right_lane = s_rgt && tx < 4;
@@ -787,8 +787,8 @@ __device__ __forceinline__ void fused_mt_run(const Src& S, const int first, cons
     }
     const Strips out = S.out(t);
     if (i0 == 0 && s_top) {
-      out.ST[(size_t)(a - 1) * g.W + c0 + j0] = lo2(P1[0][0]);
-      out.ST[(size_t)(a - 1) * g.W + c0 + j0 + 1] = lo2(P1[1][0]);
+      out.ST[(ptrdiff_t)(a - 1) * g.W + c0 + j0] = lo2(P1[0][0]);
+      out.ST[(ptrdiff_t)(a - 1) * g.W + c0 + j0 + 1] = lo2(P1[1][0]);
     }
     if (tx == 0 && s_lft) {
 #pragma unroll

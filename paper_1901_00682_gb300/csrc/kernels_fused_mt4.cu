@@ -197,16 +197,16 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
       }
     }
     if (tid < 32) {
-      if (rank == 0 && a > 0) cp_async16(smem + L::XLT + 4 * tid, A.lamh + (size_t)(a - 1) * g.W + c0 + 4 * tid);
+      if (rank == 0 && (a > 0 || g.cut_top)) cp_async16(smem + L::XLT + 4 * tid, A.lamh + (ptrdiff_t)(a - 1) * g.W + c0 + 4 * tid);
       if (tid < 4 && b > 0) cp_async16(smem + L::XLL + 4 * tid, A.lamv + (size_t)(b - 1) * g.H + gb + 4 * tid);
     } else if (tid < 64) {
       const int q = tid - 32;
-      if (rank == CL - 1 && a + 1 < g.NR)
+      if (rank == CL - 1 && (a + 1 < g.NR || g.cut_bot))
         cp_async16(smem + L::XPB + 4 * q, A.P1 + (size_t)(a * 128 + 128 + a) * g.W + c0 + 4 * q);
       if (q < 4 && b + 1 < g.NC) cp_async16(smem + L::XLR + 4 * q, A.lamv + (size_t)b * g.H + gb + 4 * q);
     } else if (tid < 96) {
       const int q = tid - 64;
-      if (rank == CL - 1 && a + 1 < g.NR) cp_async16(smem + L::XLB + 4 * q, A.lamh + (size_t)a * g.W + c0 + 4 * q);
+      if (rank == CL - 1 && (a + 1 < g.NR || g.cut_bot)) cp_async16(smem + L::XLB + 4 * q, A.lamh + (size_t)a * g.W + c0 + 4 * q);
     } else {
       const int q = tid - 96;
       if (rank < CL - 1) cp_async16(smem + L::XQH + 4 * q, A.P1 + (size_t)(gb + BAND + a) * g.W + c0 + 4 * q);
@@ -236,7 +236,7 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
     const int c0 = b * 128;
     const int gb = a * 128 + rank * BAND;
     const int o = b & 3;
-    const bool s_top = a > 0, s_bot = a + 1 < g.NR, s_lft = b > 0, s_rgt = b + 1 < g.NC;
+    const bool s_top = a > 0 || g.cut_top, s_bot = a + 1 < g.NR || g.cut_bot, s_lft = b > 0, s_rgt = b + 1 < g.NC;
     const float lim_left = (l == 0 && !s_lft) ? 0.f : 1.f;
     const float lim_top = (i0 == 0 && !s_top) ? 0.f : 1.f;
     const bool right_owner = s_rgt && l == 31;
@@ -477,7 +477,7 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
       }
     }
     if (i0 == 0 && s_top)
-      *reinterpret_cast<float4*>(A.out.ST + (size_t)(a - 1) * g.W + c0 + j0) =
+      *reinterpret_cast<float4*>(A.out.ST + (ptrdiff_t)(a - 1) * g.W + c0 + j0) =
           make_float4(lo2(P1[0][0]), lo2(P1[1][0]), lo2(P1[2][0]), lo2(P1[3][0]));
     if (last_row_here && s_bot) {
       const float4 v = *reinterpret_cast<const float4*>(smem + L::PBS + j0);

@@ -227,7 +227,29 @@ __global__ void __launch_bounds__(kBlock) k_energy_rows(int H, int W, float alph
   }
 }
 
+// sum_j |a_j - b_j| over one row pair (the anisotropic TV across the cut between two
+// row-block shards), float64, one block, fixed order
+__global__ void __launch_bounds__(kBlock) k_row_tv(const float* __restrict__ a, const float* __restrict__ b, int n,
+                                                   double* out) {
+  __shared__ double sw[kBlock / 32];
+  double v = 0.0;
+  for (int j = threadIdx.x; j < n; j += kBlock) v += fabs((double)a[j] - (double)b[j]);
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) t += sw[w];
+    *out = t;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_row_tv(const float* a, const float* b, int n, double* out, cudaStream_t st) {
+  k_row_tv<<<1, kBlock, 0, st>>>(a, b, n, out);
+  return cudaGetLastError();
+}
 
 int reduce_partials_count() { return 2 * kBlocks; }
 

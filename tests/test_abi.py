@@ -168,3 +168,20 @@ def test_product_code_never_touches_the_oracle():
     for path in glob.glob(os.path.join(pkg, "csrc", "*")):
         src = open(path).read()
         assert "dd_tv_oracle" not in src and "oracle/" not in src, path
+
+
+@pytest.mark.parametrize("rows,begin,end,path,code,needle", [
+    (512, 2, 2, "fused", "EINVAL", "nonempty range"),
+    (512, 0, 5, "fused", "EINVAL", "nonempty range"),
+    (512, -1, 2, "fused", "EINVAL", "start at 0"),
+    (502, 0, 2, "fused", "EINVAL", "equal height"),
+    (512, 0, 2, "plain", "EUNSUPPORTED", "fused path"),
+])
+def test_create_shard_rejects_invalid(lib, rows, begin, end, path, code, needle):
+    """A row-block shard is validated on the host before any device call."""
+    from paper_1901_00682_gb300 import _lib
+    p = _lib.make_params(rows, 256, 4, 2, path=path)
+    h = ctypes.c_void_p()
+    assert lib.dd_tv_create_shard(ctypes.byref(h), ctypes.byref(p), begin, end) == getattr(_lib, code)
+    assert not h.value
+    assert needle in lib.dd_tv_last_error(None).decode()
