@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched multi-image measurement")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuned time-to-accuracy")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the unrolled-adjoint measurement")
+    ap.add_argument("--replicas", action="store_true",
+                    help="with --gpus N > 1: N independent replicas instead of one sharded image")
     return ap.parse_args()
 
 
@@ -273,6 +275,98 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_sharded(args, rank, world, local, dev, stream, pg):
+    """Weak scaling of one image over `world` GPUs: 4096 * world rows x 4096 columns
+    (the ranks' 4096^2 blocks are independent synthetic scenes, seeds 0..world-1),
+    32 * world x 32 subdomains of 128^2, rank r owning tile rows [32 r, 32 r + 32).  One
+    step = one outer iteration on every rank, including the exchange of the cut strips
+    (NCCL point-to-point); the energy of the stopping rule every 5 steps adds the ranks'
+    parts (float64 all-reduce).  Returns the bench JSON fields (rank 0)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1901_00682_gb300 import _lib as L
+    from paper_1901_00682_gb300.shard import ShardedSolver, TorchDistComm
+    p = L.make_params(H * world, W, NR * world, NC, fidelity="l2", alpha=ALPHA, inner_iters=INNER, path="fused")
+    comm = TorchDistComm(pg)
+    ss = ShardedSolver(p, rank, world, comm, stream=stream)
+    r0, nrows = ss.rows()
+    assert nrows == H
+    f, _ = synth.rof_image(H, W, N_SHAPES, NOISE, SEED + rank)
+    fd = torch.from_numpy(f).to(dev)
+    ss.load(fd)
+    pg.barrier()
+    for q in range(args.warmup):
+        ss.step(1)
+        if (q + 1) % ENERGY_EVERY == 0:
+            ss.energy()
+    torch.cuda.synchronize(dev)
+    ss.solver.profile_read()
+    ss.solver.set_profiling(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    pg.barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for q in range(args.steps):
+        ss.step(1)
+        if (q + 1) % ENERGY_EVERY == 0:
+            ss.energy()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    pg.barrier()
+    clocks.stop()
+    prof_ms, prof_n = ss.solver.profile_read()
+    ss.solver.set_profiling(False)
+    t_max = max_over_ranks(e0.elapsed_time(e1), pg, dev)
+    work = H * W * INNER * args.steps
+    value = whole_job_rate(work, world, t_max * 1e-3)
+    local_avg_ms = prof_ms["local"] / max(prof_n["local"], 1)
+    smem_peak = L.measure_smem_bandwidth()
+    bytes_per_launch = SMEM_BYTES_PER_PX_ITER * H * W * INNER
+    achieved = bytes_per_launch / (local_avg_ms * 1e-3) / 1e9
+    roofline = {"bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
+                "frac": achieved / smem_peak, "traffic": None,
+                "kernel": "fused local solver of the rank's 4096x4096 block (k_fused_mt4t)",
+                "peak_source": "measured live: ld.shared probe kernel (dd_tv_measure_smem_bandwidth)",
+                "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": local_avg_ms}
+    row_tv = args.steps // ENERGY_EVERY if rank < world - 1 else 0   # the cut's TV kernel of each energy
+    # end to end: the rank's f block from pinned host memory, the steps, u back to the host
+    f_pin = torch.from_numpy(f).pin_memory()
+    u_pin = torch.empty_like(f_pin).pin_memory()
+    ud = torch.empty_like(fd)
+    pg.barrier()
+    torch.cuda.synchronize(dev)
+    t = time.perf_counter()
+    fd.copy_(f_pin, non_blocking=True)
+    ss.load(fd)
+    for q in range(args.steps):
+        ss.step(1)
+        if (q + 1) % ENERGY_EVERY == 0:
+            ss.energy()
+    ss.solver.get_u(ud)
+    u_pin.copy_(ud, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    dt_e2e = max_over_ranks(time.perf_counter() - t, pg, dev)
+    ss.solver.close()
+    e2e = {"value": whole_job_rate(work, world, dt_e2e), "unit": UNIT,
+           "h2d_bytes_per_step": 4 * H * W / args.steps, "d2h_bytes_per_step": 4 * H * W / args.steps,
+           "call": "per rank: H2D of its f block, dd_tv_load, the sharded outer iterations with the cut exchange, "
+                   "D2H of its u block"}
+    return {"value": value, "t_max": t_max, "e2e": e2e, "clocks": clocks.summary(), "roofline": roofline,
+            "phase_ms": prof_ms, "launches_by_phase": prof_n,
+            "config": {"workload": f"rof{H * world}x{W}: ROF L2 denoising {H * world}x{W} fp32 ({world} stacked "
+                                   f"4096^2 scenes), alpha=8, {NR * world}x{NC} subdomains of 128x128, 10 inner/outer",
+                       "l2": "state larger than L2; no flush",
+                       "parallelism": f"row-block shards x{world} (tile rows per rank: {NR}), cut strips exchanged "
+                                      "by NCCL point-to-point every outer iteration, energy by float64 all-reduce",
+                       "step": "1 outer iteration on every rank incl. the cut exchange, energy every 5 steps"},
+            "gpu_launches": int(sum(prof_n.values())) + row_tv}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -285,6 +379,22 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
+    if world > 1 and not args.replicas:
+        from paper_1901_00682_gb300 import _lib as L
+        L.load()
+        stream = torch.cuda.Stream(dev)
+        torch.cuda.set_stream(stream)
+        r = run_sharded(args, rank, world, local, dev, stream, pg)
+        if rank == 0:
+            print(json.dumps({
+                "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": r["t_max"] / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": r["config"],
+                "roofline": r["roofline"], "cpu_baseline": None, "e2e": r["e2e"], "clocks": r["clocks"],
+                "gpu_launches": r["gpu_launches"], "launches_by_phase": r["launches_by_phase"],
+                "phase_ms": r["phase_ms"]}), flush=True)
+        pg.destroy_process_group()
+        return
     from paper_1901_00682_gb300 import _lib as L
 
     L.load()

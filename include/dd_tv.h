@@ -376,7 +376,9 @@ long long dd_tv_batch_pixels(const dd_tv_batch* b);
  * the alpha derivative back).
  *
  * dd_tv_set_alpha changes the fidelity weight of an existing handle (same checks as
- * dd_tv_create); the next dd_tv_adjoint_forward / dd_tv_iterate use it.
+ * dd_tv_create); the next dd_tv_adjoint_forward / dd_tv_iterate use it.  A changed
+ * alpha invalidates the checkpoints of an earlier dd_tv_adjoint_forward: the next
+ * dd_tv_adjoint_backward returns DD_TV_EINVAL until a new forward pass is run.
  * dd_tv_adjoint_release frees the checkpoint, tape and adjoint memory. */
 int dd_tv_adjoint_forward(dd_tv* h, const float* f_dev, const uint8_t* mask_dev, int n_outer, int checkpoint_every,
                           float* u_dev);

@@ -9,11 +9,15 @@ order, giving dL/df and dL/dalpha for the incoming dL/du_N.
 
 Every image of a batch has its own library handle and CUDA stream; the images'
 forward and backward passes are issued from a small thread pool (the ctypes calls
-release the GIL), so they run concurrently on the GPU.  Argument marshalling only:
-all arithmetic runs in the library.
+release the GIL), so they run concurrently on the GPU.  A handle keeps the
+checkpoints of one forward pass, so every forward whose backward may still come gets
+its own set of handles: a set is lent to a forward until the autograd graph that holds
+that forward is freed (then it is reused), so several forwards may run before their
+backwards.  Argument marshalling only: all arithmetic runs in the library.
 """
 from __future__ import annotations
 
+import weakref
 from concurrent.futures import ThreadPoolExecutor
 
 import torch
@@ -33,24 +37,36 @@ class UnrolledDDTV:
         self.every = int(checkpoint_every)
         self.kw = dict(sub_rows=sub_rows, sub_cols=sub_cols, fidelity=fidelity, c1=c1, c2=c2,
                        inner_iters=inner_iters, path=path, variant=variant, **steps)
-        self._handles = []   # (Solver, torch.cuda.Stream)
+        self._sets = []      # handle sets: {"handles": [(Solver, torch.cuda.Stream)], "owner": weakref | None}
         self._pool = None
 
-    def _solvers(self, n, alpha0):
-        while len(self._handles) < n:
+    def _lend(self, n, alpha0, ctx):
+        """A handle set of at least n handles whose checkpoints no live forward needs,
+        lent to ctx (the forward's autograd context) until ctx is freed."""
+        free = None
+        for hs in self._sets:
+            if hs["owner"] is None or hs["owner"]() is None:
+                free = hs
+                break
+        if free is None:
+            free = {"handles": [], "owner": None}
+            self._sets.append(free)
+        while len(free["handles"]) < n:
             st = torch.cuda.Stream()
             p = L.make_params(*self.shape, alpha=alpha0, outer_iters=self.n_outer, **self.kw)
-            self._handles.append((L.Solver(p, st), st))
+            free["handles"].append((L.Solver(p, st), st))
+        free["owner"] = weakref.ref(ctx)
         if self._pool is None or self._pool._max_workers < n:
             if self._pool is not None:
                 self._pool.shutdown()
             self._pool = ThreadPoolExecutor(max_workers=n)
-        return self._handles[:n]
+        return free
 
     def close(self):
-        for s, _ in self._handles:
-            s.close()
-        self._handles = []
+        for hs in self._sets:
+            for s, _ in hs["handles"]:
+                s.close()
+        self._sets = []
         if self._pool is not None:
             self._pool.shutdown()
             self._pool = None
@@ -77,7 +93,8 @@ class _UnrolledFn(torch.autograd.Function):
         if len(al) not in (1, B):
             raise ValueError("alpha must be a scalar or have one entry per image")
         al = al * B if len(al) == 1 else al
-        hs = mod._solvers(B, al[0])
+        lent = mod._lend(B, al[0], ctx)
+        hs = lent["handles"][:B]
         m = None if mask is None else mask.to(torch.uint8).contiguous()
         u = torch.empty_like(f)
         cur = torch.cuda.current_stream()
@@ -96,14 +113,14 @@ class _UnrolledFn(torch.autograd.Function):
         list(mod._pool.map(fwd, range(B)))
         for _, st in hs:
             cur.wait_stream(st)
-        ctx.mod, ctx.B, ctx.alpha_shape = mod, B, alpha.shape
+        ctx.mod, ctx.B, ctx.alpha_shape, ctx.lent = mod, B, alpha.shape, lent
         ctx.alpha_dtype = alpha.dtype
         return u
 
     @staticmethod
     def backward(ctx, gu):
         mod, B = ctx.mod, ctx.B
-        hs = mod._handles[:B]
+        hs = ctx.lent["handles"][:B]
         gu = gu.contiguous().float()
         gf = torch.empty_like(gu)
         cur = torch.cuda.current_stream()

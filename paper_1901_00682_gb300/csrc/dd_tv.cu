@@ -1091,6 +1091,9 @@ int dd_tv_set_alpha(dd_tv* h, double alpha) {
   // kernels and captured graphs read the schedule from device memory at run time
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaMemcpy(h->coef, sched.data(), sched.size() * sizeof(Coef), cudaMemcpyHostToDevice));
+  // checkpoints recorded with the old alpha no longer describe the iteration that a
+  // reverse pass would recompute: dd_tv_adjoint_backward needs a new forward
+  if (h->adj && alpha != h->p.alpha) h->adj->gen = -1;
   h->p = q;
   return DD_TV_OK;
 }

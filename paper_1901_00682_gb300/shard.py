@@ -54,11 +54,14 @@ class Shard:
 
 
 class TorchDistComm:
-    """Exchange over torch.distributed (one shard per rank)."""
+    """Exchange over torch.distributed (one shard per rank).  stage_on_host: move the
+    device buffers through host copies (for a backend without device transport, such
+    as gloo; NCCL sends device memory directly)."""
 
-    def __init__(self, dist, group=None):
+    def __init__(self, dist, group=None, stage_on_host=False):
         self.dist = dist
         self.group = group
+        self.stage = stage_on_host
 
     def exchange(self, sh: Shard, sends=None, recvs=None):
         d = self.dist
@@ -66,16 +69,22 @@ class TorchDistComm:
                           (sh.send_bottom, sh.rank + 1) if sh.cut_bottom else None)
         recvs = recvs or ((sh.recv_above, sh.rank - 1) if sh.cut_top else None,
                           (sh.recv_below, sh.rank + 1) if sh.cut_bottom else None)
-        ops = []
+        ops, landing = [], []
         for t in sends:
             if t is not None:
-                ops.append(d.P2POp(d.isend, t[0], t[1], self.group))
+                buf = t[0].cpu() if self.stage else t[0]
+                ops.append(d.P2POp(d.isend, buf, t[1], self.group))
         for t in recvs:
             if t is not None:
-                ops.append(d.P2POp(d.irecv, t[0], t[1], self.group))
+                buf = t[0].new_empty(t[0].shape, device="cpu") if self.stage else t[0]
+                landing.append((t[0], buf))
+                ops.append(d.P2POp(d.irecv, buf, t[1], self.group))
         if ops:
             for w in d.batch_isend_irecv(ops):
                 w.wait()
+        if self.stage:
+            for dst, buf in landing:
+                dst.copy_(buf)
 
     def exchange_rows(self, sh: Shard):
         """Sends the first pixel row up, receives the row below (energy across a cut)."""
@@ -84,7 +93,7 @@ class TorchDistComm:
 
     def allreduce_sum(self, x: float, like=None) -> float:
         import torch
-        dev = like.device if like is not None else "cpu"
+        dev = like.device if like is not None and not self.stage else "cpu"
         t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
         self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM, group=self.group)
         return float(t.item())

@@ -197,6 +197,14 @@ def test_adjoint_errors(cuda_lib):
             s.adjoint_backward(f, u)
         with pytest.raises(L.DDTVError):
             s.set_alpha(-1.0)
+        s.adjoint_forward(f, None, 4, 2, u)
+        s.set_alpha(7.0)                         # a new alpha invalidates the checkpoints
+        with pytest.raises(L.DDTVError) as e:
+            s.adjoint_backward(f, u)
+        assert e.value.code == L.EINVAL
+        s.adjoint_forward(f, None, 4, 2, u)      # the same alpha again keeps them valid
+        s.set_alpha(7.0)
+        s.adjoint_backward(f, torch.empty_like(f))
     with L.Solver(L.make_params(32, 32, path="fulldim")) as s:
         with pytest.raises(L.DDTVError) as e:
             s.adjoint_forward(f, None, 4, 2, u)
@@ -230,6 +238,34 @@ def test_autograd_function_batch_and_alpha(cuda_lib):
         s = _gpu(fs[b], gs[b], None, 3, 2, N, "l2", every=4, alpha=float(alphas[b].detach()))
         assert np.array_equal(f.grad[b].cpu().numpy().astype(np.float64), s[1])
         assert alphas.grad[b].item() == s[2]
+    mod.close()
+
+
+def test_autograd_two_forwards_before_their_backwards(cuda_lib):
+    """Two calls of the module before either backward (each forward keeps its own
+    checkpoints): each backward, in either order, gives the single-call gradients."""
+    from paper_1901_00682_gb300.autograd import UnrolledDDTV
+    B, H, W, N = 2, 48, 40, 6
+    cases = [[_case(H, W, "l2", 0.0, seed=30 + 10 * k + b)[:2] for b in range(B)] for k in range(2)]
+    mod = UnrolledDDTV(H, W, 3, 2, N, checkpoint_every=4)
+    fs, losses, alphas = [], [], []
+    for k in range(2):
+        f = torch.from_numpy(np.stack([c[0] for c in cases[k]])).cuda().requires_grad_(True)
+        g = torch.from_numpy(np.stack([c[1] for c in cases[k]])).cuda()
+        a = torch.tensor(10.0 + k, dtype=torch.float64, device="cuda", requires_grad=True)
+        u = mod(f, a)
+        fs.append(f)
+        alphas.append(a)
+        losses.append(0.5 * ((u - g) ** 2).sum())
+    losses[1].backward()
+    losses[0].backward()
+    for k in range(2):
+        for b in range(B):
+            s = _gpu(cases[k][b][0], cases[k][b][1], None, 3, 2, N, "l2", every=4, alpha=10.0 + k)
+            assert np.array_equal(fs[k].grad[b].cpu().numpy().astype(np.float64), s[1]), (k, b)
+        want = sum(_gpu(cases[k][b][0], cases[k][b][1], None, 3, 2, N, "l2", every=4, alpha=10.0 + k)[2]
+                   for b in range(B))
+        assert abs(alphas[k].grad.item() - want) <= 1e-12 * abs(want)
     mod.close()
 
 

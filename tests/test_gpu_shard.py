@@ -7,6 +7,9 @@ to J of the whole image; and the sharded run matches the FP64 oracle at equal
 iteration counts.  Several shards share the one GPU here as separate launches that do
 not wait on one another (the exchange is a copy between launches)."""
 import ctypes
+import os
+import socket
+import sys
 
 import numpy as np
 import pytest
@@ -131,3 +134,62 @@ def test_shard_refuses_whole_state_calls_and_bad_ranges():
     assert lib.dd_tv_create_shard(ctypes.byref(h), ctypes.byref(q), 0, 2) == L.EINVAL
     q = L.make_params(512, 256, 4, 2, path="plain")
     assert lib.dd_tv_create_shard(ctypes.byref(h), ctypes.byref(q), 0, 2) == L.EUNSUPPORTED
+
+
+def _free_port():
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def _rank_worker(rank, world, port, H, W, NR, NC, n_outer, out):
+    """One process per shard, all on cuda:0, exchanging through gloo with host staging
+    (their kernels never wait on one another: every exchange happens between launches)."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import torch.distributed as dist
+
+    import synth as sy
+    from paper_1901_00682_gb300 import _lib as L
+    from paper_1901_00682_gb300.shard import ShardedSolver, TorchDistComm
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        torch.cuda.set_device(0)
+        p = L.make_params(H, W, NR, NC, fidelity="l2", alpha=8.0, inner_iters=10)
+        ss = ShardedSolver(p, rank, world, TorchDistComm(dist, stage_on_host=True))
+        f, _ = sy.rof_image(H, W, 20, 0.1, 9)
+        r0, n = ss.rows()
+        ss.load(torch.from_numpy(np.ascontiguousarray(f[r0:r0 + n])).cuda())
+        ss.step(n_outer)
+        J = ss.energy()
+        u = torch.empty(n, W, device="cuda")
+        ss.solver.get_u(u)
+        torch.cuda.synchronize()
+        out[rank] = (r0, u.cpu().numpy().tobytes(), J)
+        ss.solver.close()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_solver_over_torch_distributed_ranks():
+    """The distributed path end to end (ShardedSolver + TorchDistComm, one process per
+    shard): three ranks reproduce the single-handle run bit for bit."""
+    L = _lib()
+    import torch.multiprocessing as mp
+    H, W, NR, NC, world, n_outer = 768, 512, 6, 4, 3, 8
+    f, _ = synth.rof_image(H, W, 20, 0.1, 9)
+    p = L.make_params(H, W, NR, NC, fidelity="l2", alpha=8.0, inner_iters=10)
+    fd = torch.from_numpy(f).cuda()
+    with L.Solver(p) as s:
+        s.load(fd)
+        s.iterate(n_outer)
+        u1 = s.get_u(torch.empty_like(fd)).cpu().numpy()
+        J1 = s.current_energy()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.spawn(_rank_worker, args=(world, _free_port(), H, W, NR, NC, n_outer, out), nprocs=world, join=True)
+    for r in range(world):
+        r0, ub, J = out[r]
+        u = np.frombuffer(ub, dtype=np.float32).reshape(-1, W)
+        assert np.array_equal(u, u1[r0:r0 + u.shape[0]]), r
+        assert abs(J - J1) <= 1e-7 * abs(J1)

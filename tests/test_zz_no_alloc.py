@@ -12,6 +12,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 torch = pytest.importorskip("torch")
@@ -32,12 +33,15 @@ def test_noalloc_energy_matches_handle_energy_on_two_calls_in_a_row():
     from paper_1901_00682_gb300 import _lib as L
     lib = L.load()
     stream = torch.cuda.current_stream().cuda_stream
+    tv_f, tv_mask, _ = synth.tvl1_inpaint_image(256, 192, 12, 0.1, 0.2, 22)
     cases = [
+        # odd width: the per-pixel reduction kernel
         (synth.rof_image(300, 517, 20, 0.05, 21)[0], None, L.L2, 8.0, 0.0, 0.0),
-        (synth.tvl1_inpaint_image(256, 192, 12, 0.1, 0.2, 22)[0], synth.tvl1_inpaint_image(256, 192, 12, 0.1, 0.2, 22)[1],
-         L.L1, 1.5, 0.0, 0.0),
+        # width a multiple of 4 with a mask, then without: the two row-kernel instances
+        (tv_f, tv_mask, L.L1, 1.5, 0.0, 0.0),
+        (synth.rof_image(200, 320, 15, 0.05, 23)[0], None, L.SEG, 20.0, 0.2, 0.8),
     ]
-    for f, mask, fid, alpha, c1, c2 in cases:   # two calls in a row, different images
+    for f, mask, fid, alpha, c1, c2 in cases:   # calls in a row, different images
         H, W = f.shape
         rng = np.random.default_rng(H)
         u = torch.from_numpy((f + 0.02 * rng.standard_normal(f.shape)).astype(np.float32)).cuda()
@@ -49,6 +53,11 @@ def test_noalloc_energy_matches_handle_energy_on_two_calls_in_a_row():
         J_ref = s.energy(u, fd, md)
         s.close()
         assert abs(J - J_ref) <= 1e-6 * abs(J_ref), (J, J_ref)
+        # and against the FP64 oracle's energy of the same float32 arrays
+        fidname = {L.L2: "l2", L.L1: "l1", L.SEG: "seg"}[fid]
+        pr = oracle.Problem(H, W, fidelity=fidname, alpha=alpha, c1=c1, c2=c2)
+        Jo = oracle.energy(pr, u.cpu().numpy().astype(np.float64), f.astype(np.float64), mask)
+        assert abs(J - Jo) <= 1e-5 * abs(Jo), (J, Jo)
 
 
 def test_noalloc_energy_rejects_bad_sizes():
