@@ -305,13 +305,15 @@ int dd_tv_shard_energy(dd_tv* h, const float* row_below_dev, double* J_out);
  * batch is two kernel launches (multiplier update of every interface of every image,
  * then the local solves of every subdomain of every image: by default a persistent
  * kernel whose clusters walk the batch's work list of (image, subdomain) pairs with
- * each image's fidelity and parameters), replayed as a CUDA graph.
- * Image sides must be multiples of the subdomain side (128).  Results are bit-identical
- * to solving each image alone with the same parameters. */
+ * each image's fidelity and parameters).  dd_tv_batch_iterate(b, n) with n > 1 is one
+ * CUDA-graph launch of the n outer iterations (the graph is captured on the first call
+ * with that n and start parity and replayed by later ones).
+ * Image sides must be multiples of the subdomain side (64 or 128).  Results are
+ * bit-identical to solving each image alone with the same parameters. */
 typedef struct dd_tv_batch dd_tv_batch;
 
 typedef struct {
-  int height, width;      /* multiples of 128                                          */
+  int height, width;      /* multiples of the subdomain side                           */
   int fidelity;           /* DD_TV_L2, DD_TV_L1 or DD_TV_SEG (no inpainting mask)        */
   double alpha, c1, c2;   /* as in dd_tv_params                                        */
   double tau, sigma;      /* outer steps; tau <= 0 selects Section 5's defaults: tau = 50
@@ -319,7 +321,9 @@ typedef struct {
 } dd_tv_batch_image;
 
 typedef struct {
-  int tile;               /* subdomain side; 128 is the only value supported             */
+  int tile;               /* subdomain side: 128 (persistent clusters of 2 x 4 pixel
+                             micro-tiles over the work list) or 64 (one CTA per
+                             subdomain); other sides return DD_TV_EUNSUPPORTED          */
   int inner_iters;        /* 1..DD_TV_MAX_INNER                                        */
   double tau0, sigma0;    /* initial inner steps (Section 5: 10 and 1/80)               */
   int variant;            /* must be 0: persistent clusters over the batch's work list,

@@ -390,15 +390,16 @@ class Batch:
     images: list of dicts with height, width, fidelity ("l2", "l1", "seg" or code),
     alpha, c1, c2 and optionally tau, sigma (defaults: the paper's per fidelity)."""
 
-    def __init__(self, images, inner_iters=10, tau0=10.0, sigma0=None, variant=0, stream=None):
+    def __init__(self, images, inner_iters=10, tau0=10.0, sigma0=None, variant=0, stream=None, tile=128):
         self.lib = load()
+        self.tile = tile
         n = len(images)
         arr = (BatchImage * n)()
         for k, im in enumerate(images):
             fid = {"l2": L2, "l1": L1, "seg": SEG}.get(im.get("fidelity", L2), im.get("fidelity", L2))
             arr[k] = BatchImage(im["height"], im["width"], fid, im.get("alpha", 10.0), im.get("c1", 0.0),
                                 im.get("c2", 0.0), im.get("tau", 0.0), im.get("sigma", 0.0))
-        bp = BatchParams(128, inner_iters, tau0, sigma0 if sigma0 is not None else 0.125 / tau0, variant)
+        bp = BatchParams(tile, inner_iters, tau0, sigma0 if sigma0 is not None else 0.125 / tau0, variant)
         h = ctypes.c_void_p()
         _bcheck(self.lib.dd_tv_batch_create(ctypes.byref(h), arr, n, ctypes.byref(bp)), None)
         self.h = h

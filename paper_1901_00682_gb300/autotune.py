@@ -115,10 +115,11 @@ def tune(f, problem, tol=1e-4, j_ref=None, tiles=(64, 128), inners=(5, 10, 20), 
     return TuneResult(best, trials, j_ref, tol)
 
 
-def batch_reference_energies(images, fs, inner=20, outer=2000, variant=0, stream=None):
+def batch_reference_energies(images, fs, inner=20, outer=2000, stream=None):
     """Lowest energy of every image of a batch over a long batched run (upper bounds
-    of the images' J*).  images: dicts as for _lib.Batch; fs: device tensors."""
-    b = L.Batch(images, inner_iters=inner, variant=variant, stream=stream)
+    of the images' J*, for batches without a certified reference).  images: dicts as for
+    _lib.Batch; fs: device tensors."""
+    b = L.Batch(images, inner_iters=inner, stream=stream)
     b.load(fs)
     best = [math.inf] * len(images)
     step = max(outer // 20, 1)
@@ -130,12 +131,14 @@ def batch_reference_energies(images, fs, inner=20, outer=2000, variant=0, stream
     return best
 
 
-def _batch_trial(images, fs, inner, variant, j_ref, tol, max_outer, check_every, stream):
+def _batch_trial(images, fs, tile, inner, j_ref, tol, max_outer, check_every, stream):
     """Device time (CUDA events around the outer iterations only) until every image's
     relative energy error (J - J*)/|J*| is <= tol, checked every check_every outer
     iterations; the batch advances all images together."""
     import torch
-    b = L.Batch(images, inner_iters=inner, variant=variant, stream=stream)
+    if any(im["height"] % tile or im["width"] % tile for im in images):
+        return Trial(tile, inner, 0, math.inf, 0, math.inf, False)
+    b = L.Batch(images, inner_iters=inner, stream=stream, tile=tile)
     st = torch.cuda.current_stream() if stream is None else stream
     b.load(fs)
     b.iterate(4)                      # warm-up: graph capture
@@ -154,25 +157,25 @@ def _batch_trial(images, fs, inner, variant, j_ref, tol, max_outer, check_every,
             break
     b.close()
     reached = worst <= tol
-    return Trial(128, inner, variant, ms if reached else math.inf, done, worst, reached)
+    return Trial(tile, inner, 0, ms if reached else math.inf, done, worst, reached)
 
 
-def tune_batch(images, fs, tol=1e-4, j_ref=None, inners=(5, 10, 20), variants=(0,), max_outer=3000,
+def tune_batch(images, fs, tol=1e-4, j_ref=None, inners=(5, 10, 20), tiles=(64, 128), max_outer=3000,
                check_every=10, stream=None, solve_fn=None):
-    """Chooses the inner-iteration count K and the hardware mapping of a batched solve
-    (subdomain side 128) by the measured device time until every image of the batch
-    reaches relative energy error tol.  j_ref: per-image J* (estimated by
-    batch_reference_energies when None).  solve_fn(inner, variant, j_ref) -> Trial
+    """Chooses the subdomain side and the inner-iteration count K of a batched solve by
+    the measured device time until every image of the batch reaches relative energy
+    error tol.  j_ref: per-image J* (certified values, or estimated by
+    batch_reference_energies when None).  solve_fn(tile, inner, j_ref) -> Trial
     replaces the GPU measurement (host-side tests)."""
     if j_ref is None and solve_fn is None:
         j_ref = batch_reference_energies(images, fs, stream=stream)
     trials = []
-    for inner in inners:
-        for v in variants:
+    for tile in tiles:
+        for inner in inners:
             if solve_fn is not None:
-                trials.append(solve_fn(inner, v, j_ref))
+                trials.append(solve_fn(tile, inner, j_ref))
             else:
-                trials.append(_batch_trial(images, fs, inner, v, j_ref, tol, max_outer, check_every, stream))
+                trials.append(_batch_trial(images, fs, tile, inner, j_ref, tol, max_outer, check_every, stream))
     return TuneResult(pick_best(trials), trials, j_ref, tol)
 
 

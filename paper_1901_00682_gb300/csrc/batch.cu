@@ -16,7 +16,7 @@ using namespace ddtv;
 
 namespace {
 thread_local char g_batch_create_err[512] = {0};
-constexpr int kBatchChunk = 4;
+constexpr int kMaxGraphs = 8;  // captured run lengths kept per batch (least recently used dropped)
 }  // namespace
 
 struct dd_tv_batch {
@@ -42,7 +42,15 @@ struct dd_tv_batch {
   cudaStream_t stream = nullptr, own = nullptr;
   int outer = 0;
   bool loaded = false;
-  cudaGraphExec_t chunk[2] = {nullptr, nullptr};
+  // one CUDA graph per (outer iterations, start parity) of dd_tv_batch_iterate calls:
+  // a call of n > 1 outer iterations is one graph launch
+  struct Run {
+    int count, par;
+    cudaGraphExec_t exec;
+    long long used;
+  };
+  std::vector<Run> graphs;
+  long long tick = 0;
   char err[512] = {0};
 };
 
@@ -100,40 +108,52 @@ cudaError_t outer_once(dd_tv_batch* b, int par) {
   ba.tile_img = b->d_tile_img;
   ba.tile_base = b->d_tile_base;
   ba.write_set = 1 - par;
-  return launch_fused_batch(ba, b->total_tiles, b->p.variant, b->stream);
+  return launch_fused_batch(ba, b->total_tiles, b->p.tile, b->stream);
+}
+
+void drop_batch_graphs(dd_tv_batch* b) {
+  for (auto& r : b->graphs) cudaGraphExecDestroy(r.exec);
+  b->graphs.clear();
 }
 
 int run(dd_tv_batch* b, int count) {
-  int done = 0;
-  while (done < count) {
-    const int par = b->outer & 1;
-    if (count - done >= kBatchChunk) {
-      if (!b->chunk[par]) {
-        cudaGraph_t graph = nullptr;
-        BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = cudaSuccess;
-        for (int q = 0; q < kBatchChunk && e == cudaSuccess; ++q) e = outer_once(b, (par + q) & 1);
-        cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
-        if (e != cudaSuccess || e2 != cudaSuccess) {
-          if (graph) cudaGraphDestroy(graph);
-          return bfail(b, DD_TV_ECUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
-        }
-        e = cudaGraphInstantiate(&b->chunk[par], graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) {
-          b->chunk[par] = nullptr;
-          return bfail(b, DD_TV_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
-        }
-      }
-      BCK(cudaGraphLaunch(b->chunk[par], b->stream));
-      b->outer += kBatchChunk;
-      done += kBatchChunk;
-    } else {
-      BCK(outer_once(b, par));
-      b->outer += 1;
-      done += 1;
-    }
+  if (count <= 0) return DD_TV_OK;
+  const int par = b->outer & 1;
+  if (count == 1) {
+    BCK(outer_once(b, par));
+    b->outer += 1;
+    return DD_TV_OK;
   }
+  cudaGraphExec_t exec = nullptr;
+  for (auto& r : b->graphs)
+    if (r.count == count && r.par == par) {
+      exec = r.exec;
+      r.used = ++b->tick;
+    }
+  if (!exec) {
+    cudaGraph_t graph = nullptr;
+    BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < count && e == cudaSuccess; ++q) e = outer_once(b, (par + q) & 1);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return bfail(b, DD_TV_ECUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return bfail(b, DD_TV_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    if ((int)b->graphs.size() >= kMaxGraphs) {  // drop the least recently used run length
+      size_t lru = 0;
+      for (size_t q = 1; q < b->graphs.size(); ++q)
+        if (b->graphs[q].used < b->graphs[lru].used) lru = q;
+      cudaGraphExecDestroy(b->graphs[lru].exec);
+      b->graphs.erase(b->graphs.begin() + lru);
+    }
+    b->graphs.push_back(dd_tv_batch::Run{count, par, exec, ++b->tick});
+  }
+  BCK(cudaGraphLaunch(exec, b->stream));
+  b->outer += count;
   return DD_TV_OK;
 }
 
@@ -146,16 +166,18 @@ int dd_tv_batch_create(dd_tv_batch** out, const dd_tv_batch_image* images, int n
   *out = nullptr;
   dd_tv_batch* b = nullptr;
   if (!images || n < 1 || !p) return bfail(nullptr, DD_TV_EINVAL, "need n >= 1 images and params");
-  if (p->tile != 128) return bfail(nullptr, DD_TV_EUNSUPPORTED, "batched subdomain side must be 128");
+  if (p->tile != 128 && p->tile != 64)
+    return bfail(nullptr, DD_TV_EUNSUPPORTED, "batched subdomain side must be 64 or 128 (got %d)", p->tile);
+  const int T = p->tile;
   if (p->inner_iters < 1 || p->inner_iters > DD_TV_MAX_INNER) return bfail(nullptr, DD_TV_EINVAL, "bad inner_iters");
   if (!(p->tau0 > 0) || !(p->sigma0 > 0) || p->tau0 * p->sigma0 > 0.125 * (1 + 1e-12))
     return bfail(nullptr, DD_TV_EINVAL, "tau0, sigma0 must be > 0 with tau0 sigma0 <= 1/8");
   if (p->variant != 0) return bfail(nullptr, DD_TV_EINVAL, "batch variant must be 0");
   for (int i = 0; i < n; ++i) {
     const dd_tv_batch_image& m = images[i];
-    if (m.height < 128 || m.width < 128 || m.height % 128 || m.width % 128)
-      return bfail(nullptr, DD_TV_EINVAL, "image %d: sides must be positive multiples of 128 (got %d x %d)", i,
-                   m.height, m.width);
+    if (m.height < T || m.width < T || m.height % T || m.width % T)
+      return bfail(nullptr, DD_TV_EINVAL, "image %d: sides must be positive multiples of the subdomain side %d (got "
+                   "%d x %d)", i, T, m.height, m.width);
     if (m.fidelity < DD_TV_L2 || m.fidelity > DD_TV_SEG) return bfail(nullptr, DD_TV_EINVAL, "image %d: fidelity", i);
     if (!(m.alpha > 0) || !std::isfinite(m.alpha)) return bfail(nullptr, DD_TV_EINVAL, "image %d: alpha", i);
     if (m.tau > 0 && (!(m.sigma > 0) || m.tau * m.sigma > 0.5 * (1 + 1e-12)))
@@ -179,7 +201,7 @@ int dd_tv_batch_create(dd_tv_batch** out, const dd_tv_batch_image* images, int n
   size_t at = 0;
   for (int i = 0; i < n; ++i) {
     const dd_tv_batch_image& m = b->img[i];
-    const int NR = m.height / 128, NC = m.width / 128;
+    const int NR = m.height / T, NC = m.width / T;
     const size_t npx = (size_t)m.height * m.width, n1 = (size_t)(m.height + NR) * m.width,
                  n2 = (size_t)m.height * (m.width + NC), nh = (size_t)(NR - 1) * m.width, nv = (size_t)(NC - 1) * m.height;
     off_f[i] = at; at = align_up(at + 4 * npx);
@@ -209,7 +231,7 @@ int dd_tv_batch_create(dd_tv_batch** out, const dd_tv_batch_image* images, int n
   int tb = 0, eb = 0;
   for (int i = 0; i < n; ++i) {
     const dd_tv_batch_image& m = b->img[i];
-    const int NR = m.height / 128, NC = m.width / 128;
+    const int NR = m.height / T, NC = m.width / T;
     const size_t nh = (size_t)(NR - 1) * m.width, nv = (size_t)(NC - 1) * m.height;
     const double tau = m.tau > 0 ? m.tau : (m.fidelity == DD_TV_SEG ? 1.0 : 50.0);
     const double sigma = m.tau > 0 ? m.sigma : 0.5 / tau;
@@ -289,8 +311,7 @@ int dd_tv_batch_create(dd_tv_batch** out, const dd_tv_batch_image* images, int n
 
 int dd_tv_batch_destroy(dd_tv_batch* b) {
   if (!b) return DD_TV_OK;
-  for (auto& g : b->chunk)
-    if (g) cudaGraphExecDestroy(g);
+  drop_batch_graphs(b);
   void* bufs[] = {b->arena, b->d_args, b->d_strips, b->d_fid, b->d_tile_img, b->d_tile_base, b->d_elem_base,
                   b->d_sigma, b->d_err, b->partials, b->counter, b->red_out};
   for (void* q : bufs)

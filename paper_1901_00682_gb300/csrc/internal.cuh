@@ -104,8 +104,10 @@ cudaError_t launch_scatter_strips(const Grid& g, Strips s, float* P1, float* P2,
 cudaError_t launch_interface_batch(const BatchIfaceArgs& a, int total4, cudaStream_t st);
 
 // ---- kernels_fused.cu
-// All tiles of all images of a batch, one launch (BatchArgs.write_set selects the strips).
-cudaError_t launch_fused_batch(const BatchArgs& B, int total_tiles, int variant, cudaStream_t st);
+// All tiles of all images of a batch, one launch (BatchArgs.write_set selects the strips);
+// tile: the subdomain side, 128 (persistent 2 x 4 micro-tile kernel) or 64 (one CTA per
+// subdomain).
+cudaError_t launch_fused_batch(const BatchArgs& B, int total_tiles, int tile, cudaStream_t st);
 // One outer iteration's local solves, all tiles, fused (returns cudaErrorInvalidValue
 // if no fused configuration fits the tile shape).
 cudaError_t launch_fused_local(const LocalArgs& a, int fidelity, int variant, cudaStream_t st);

@@ -56,8 +56,9 @@ struct SmemLayout {
 // all CTAs of the tile take the same decision.  (Float64 work stays with one thread:
 // the float64 pipe of this GPU is narrow.)  The u-step's first cluster wait is then
 // taken at the end of the previous iteration's p-step instead.
+// The local solve of tile (a, b) of the problem A, its interface strips written to out.
 template <int BW, int R, int TR, int CL, int FID, bool MASK, bool ADAPT>
-__global__ void __launch_bounds__(BW* TR, (BW * TR <= 256 ? 2 : 1)) k_fused(const LocalArgs A) {
+__device__ __forceinline__ void fused_tile(const LocalArgs& A, const Strips out, const int a, const int b) {
   using L = SmemLayout<BW, R, TR>;
   constexpr int BAND = L::BAND;
   extern __shared__ float smem[];
@@ -75,7 +76,6 @@ __global__ void __launch_bounds__(BW* TR, (BW * TR <= 256 ? 2 : 1)) k_fused(cons
 
   const Grid g = A.g;
   const int rank = CL > 1 ? (int)blockIdx.x : 0;
-  const int b = blockIdx.y, a = blockIdx.z;
   const int r0 = part_start(a, g.H, g.NR), mr = part_start(a + 1, g.H, g.NR) - r0;
   const int c0 = part_start(b, g.W, g.NC), mc = part_start(b + 1, g.W, g.NC) - c0;
   const bool s_top = a > 0 || g.cut_top, s_bot = a + 1 < g.NR || g.cut_bot, s_lft = b > 0, s_rgt = b + 1 < g.NC;
@@ -309,18 +309,41 @@ __global__ void __launch_bounds__(BW* TR, (BW * TR <= 256 ? 2 : 1)) k_fused(cons
       A.u[(size_t)gi * g.W + gj] = u[r];
       A.P1[(size_t)(gi + a) * g.W + gj] = p1[r];
       A.P2[(size_t)gi * W2 + gj + b] = p2[r];
-      if (i == 0 && s_top) A.out.ST[(ptrdiff_t)(a - 1) * g.W + gj] = p1[r];
-      if (j == 0 && s_lft) A.out.SL[(size_t)(b - 1) * g.H + gi] = p2[r];
+      if (i == 0 && s_top) out.ST[(ptrdiff_t)(a - 1) * g.W + gj] = p1[r];
+      if (j == 0 && s_lft) out.SL[(size_t)(b - 1) * g.H + gi] = p2[r];
       if (i == mr - 1 && s_bot) {
         A.P1[(size_t)(gi + a + 1) * g.W + gj] = pB;
-        A.out.SB[(size_t)a * g.W + gj] = pB;
+        out.SB[(size_t)a * g.W + gj] = pB;
       }
       if (j == mc - 1 && s_rgt) {
         const float pr = sPR[lr0 + r];
         A.P2[(size_t)gi * W2 + gj + b + 1] = pr;
-        A.out.SR[(size_t)b * g.H + gi] = pr;
+        out.SR[(size_t)b * g.H + gi] = pr;
       }
     }
+  }
+}
+
+
+template <int BW, int R, int TR, int CL, int FID, bool MASK, bool ADAPT>
+__global__ void __launch_bounds__(BW* TR, (BW * TR <= 256 ? 2 : 1)) k_fused(const LocalArgs A) {
+  fused_tile<BW, R, TR, CL, FID, MASK, ADAPT>(A, A.out, (int)blockIdx.z, (int)blockIdx.y);
+}
+
+// Every tile of a batch of images, one CTA cluster per tile (blockIdx.y = the batch's
+// tile), each with its image's fidelity, parameters and strips.
+template <int BW, int R, int TR, int CL>
+__global__ void __launch_bounds__(BW* TR, (BW * TR <= 256 ? 2 : 1)) k_fused_tile_batch(const BatchArgs B) {
+  const int t = blockIdx.y;
+  const int img = B.tile_img[t];
+  const LocalArgs A = B.args[img];
+  const int q = t - B.tile_base[img];
+  const int a = q / A.g.NC, b = q - a * A.g.NC;
+  const Strips out = B.strips[2 * img + B.write_set];
+  switch (B.fid[img]) {
+    case FID_L2: fused_tile<BW, R, TR, CL, FID_L2, false, false>(A, out, a, b); break;
+    case FID_L1: fused_tile<BW, R, TR, CL, FID_L1, false, false>(A, out, a, b); break;
+    default: fused_tile<BW, R, TR, CL, FID_SEG, false, false>(A, out, a, b); break;
   }
 }
 
@@ -438,14 +461,20 @@ cudaError_t fused_prepare() {
   cudaError_t e;
   if ((e = prepare_fid<32, 8, 4, 1>()) != cudaSuccess) return e;
   if ((e = prepare_fid<64, 8, 8, 1>()) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_fused_tile_batch<64, 8, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)SmemLayout<64, 8, 8>::BYTES)) != cudaSuccess)
+    return e;
   if ((e = prepare_fid<128, 8, 2, 8>()) != cudaSuccess) return e;
   if ((e = fused_mt_prepare()) != cudaSuccess) return e;
   return fused_mt4_prepare();
 }
 
-cudaError_t launch_fused_batch(const BatchArgs& B, int total_tiles, int variant, cudaStream_t st) {
-  (void)variant;
-  return launch_fused_mt_batch(B, total_tiles, st);
+cudaError_t launch_fused_batch(const BatchArgs& B, int total_tiles, int tile, cudaStream_t st) {
+  if (tile == 128) return launch_fused_mt_batch(B, total_tiles, st);
+  if (tile != 64) return cudaErrorInvalidValue;
+  // 64 x 64 subdomains: one CTA of 64 x 8 threads per subdomain
+  k_fused_tile_batch<64, 8, 8, 1><<<dim3(1, total_tiles, 1), dim3(64, 8, 1), SmemLayout<64, 8, 8>::BYTES, st>>>(B);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fused_local(const LocalArgs& a, int fid, int variant, cudaStream_t st) {

@@ -60,23 +60,23 @@ struct Mt4Layout {
   static constexpr int XLT = SP2 + BAND * P2S;       // lamh above the tile (128)
   static constexpr int XPB = XLT + BW;               // p1 of the tile's bottom side (128)
   static constexpr int XLB = XPB + BW;               // lamh below the tile (128)
-  static constexpr int XQH = XLB + BW;               // p1 of the first row below the band (128)
+  static constexpr int XQH = XLB + BW;               // p1 of the first row below the band (128); in the
+                                                     // last CTA, which has no band below: u of the tile's last row
   static constexpr int XLL = XQH + BW;               // lamv left of the band rows (BAND)
   static constexpr int XLR = XLL + BAND;             // lamv right of the band rows (BAND)
   static constexpr int PBS = XLR + BAND;             // bottom side p of the tile (128; last CTA)
   static constexpr int HBS = PBS + BW;               // bottom side phat (128)
-  static constexpr int HRS = HBS + BW;               // right side phat per warp (NW x 4, pair order)
-  static constexpr int MB = HRS + 4 * NW;            // two mbarriers
+  static constexpr int MB = HBS + BW;                // two mbarriers
   static constexpr size_t BYTES = sizeof(float) * MB + 16;
   // tensor-copy variant: out-buffers of u and p1 (128-byte aligned), three mbarriers
-  static constexpr int OU = (HRS + 4 * NW + 31) & ~31;
+  static constexpr int OU = (HBS + BW + 31) & ~31;
   static constexpr int OP1 = OU + BAND * BW;
   static constexpr int MBT = OP1 + BAND * BW;
   static constexpr size_t BYTES_TMA = sizeof(float) * MBT + 32;
   static constexpr uint32_t kTmaBytes = 4 * (3 * BAND * BW + BAND * P2S);  // one subdomain's four tensor loads
   static_assert(Q1 % 4 == 0 && UR % 4 == 0 && QL % 4 == 0 && F % 4 == 0 && CO % 4 == 0 && SU % 4 == 0 &&
                     SP2 % 4 == 0 && XLT % 4 == 0 && XLL % 4 == 0 && XLR % 4 == 0 && PBS % 4 == 0 &&
-                    HBS % 4 == 0 && HRS % 4 == 0 && MB % 2 == 0,
+                    HBS % 4 == 0 && MB % 2 == 0,
                 "16-byte alignment of the vector and cp.async buffers");
   static_assert(CL * BAND == 128, "a cluster of CTAs covers the 128 rows of a tile");
   static_assert(SU % 32 == 0 && SP2 % 32 == 0 && (BAND * BW) % 32 == 0 && OU % 32 == 0 && OP1 % 32 == 0,
@@ -132,6 +132,10 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
   const float tau = A.tau;
   const int K = A.K;
   const bool last_row_here = rank == CL - 1 && w == NW - 1;
+  // the tile's bottom side is updated by warp 2 of the last CTA (the last warp, which
+  // holds the last row, already waits for halos and pushes rows); warp 1 updates the
+  // right side
+  const bool bottom_warp = rank == CL - 1 && w == 2;
   const bool push_down = w == NW - 1 && rank + 1 < CL;  // sends u of the band's last row
   const bool push_up = w == 0 && rank > 0;              // sends pbar1 of the band's first row
   const bool need_uh = push_up;
@@ -155,7 +159,7 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
     if (TMA) mbar_init(mbL, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int q = tid; q < 8 * min(K, L::kMaxSmemCoef); q += NT) sCo[q] = reinterpret_cast<const float*>(A.coef)[q];
+  for (int q = tid; q < 8 * K; q += NT) sCo[q] = reinterpret_cast<const float*>(A.coef)[q];  // K <= kMaxSmemCoef
   if (rank == 0 && w == 0) *reinterpret_cast<float4*>(sUB + j0) = make_float4(0.f, 0.f, 0.f, 0.f);  // u above the tile
   if (l < 4) smem[L::UR + w * L::SLOT + l] = 0.f;  // u left of the tile
   __syncthreads();
@@ -239,10 +243,16 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
     const bool s_top = a > 0 || g.cut_top, s_bot = a + 1 < g.NR || g.cut_bot, s_lft = b > 0, s_rgt = b + 1 < g.NC;
     const float lim_left = (l == 0 && !s_lft) ? 0.f : 1.f;
     const float lim_top = (i0 == 0 && !s_top) ? 0.f : 1.f;
-    const bool right_owner = s_rgt && l == 31;
+    // The tile's right side (the p2 dofs of column 128, one per band row) is updated by
+    // lanes 0..15 of warp 1, lane i for band row i, which keeps its p and proximal
+    // centre in registers; it reads the u of column 127 from the UR slot after lane 31's
+    // and writes pbar into the QL slot after lane 31's, where lane 31 reads its right
+    // neighbour's left edge.  Slot entries are in pair order: rows (0, 2, 1, 3).
+    const bool right_rows = s_rgt && w == 1 && l < BAND;
+    const int r_slot = (l >> 2) * L::SLOT + 4 * 32 + 2 * (l & 1) + ((l >> 1) & 1);
+    float pr_s = 0.f, hr_s = 0.f;
     // pairs [column c][e]: rows (e, e + 2) of column j0 + c
     f32x2 U[4][2], P1[4][2], P2[4][2], H1[4][2], H2[4][2], Q1[4][2], Q2[4][2];
-    f32x2 PR[2] = {0ull, 0ull}, QR[2] = {0ull, 0ull};  // right side p, pbar (lane 31; phat in shared memory)
     uint32_t in_d = 0;  // bit 4c + r: pixel (row r, column j0 + c) lies in the inpainting domain
 
     cp_async_wait_all();
@@ -325,32 +335,28 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
       }
       if (need_qh)
         *reinterpret_cast<float4*>(sQ1 + NW * BW + j0) = *reinterpret_cast<const float4*>(smem + L::XQH + j0);
-      if (right_owner) {
-        float pr[4], hr[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          pr[r] = smem[L::SP2 + (lr0 + r) * L::P2S + o + 128];
-          hr[r] = phat_s(pr[r], smem[L::XLR + lr0 + r], tau);
+      if (w == 1 && l < BAND) {
+        float q = 0.f;  // an inactive right side (image boundary) reads as 0
+        if (s_rgt) {
+          pr_s = smem[L::SP2 + l * L::P2S + o + 128];
+          hr_s = phat_s(pr_s, smem[L::XLR + l], tau);
+          q = pr_s;
         }
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          PR[e] = pk2(pr[e], pr[e + 2]);
-          QR[e] = PR[e];
-        }
-        *reinterpret_cast<ulonglong2*>(smem + L::HRS + 4 * w) = make_ulonglong2(pk2(hr[0], hr[2]), pk2(hr[1], hr[3]));
+        smem[L::QL + r_slot] = q;
       }
     }
     __syncthreads();  // staging consumed by every thread
     if (t + stride < T) prefetch(t + stride);
 
+    // unrolled by two: the new dual values then land in the registers the old ones of
+    // the previous iteration held, instead of being moved back every iteration
+#pragma unroll 2
     for (int k = 0; k < K; ++k) {
       Coef co;
-      if (k < L::kMaxSmemCoef) {
+      {
         const float4 ca = *reinterpret_cast<const float4*>(sCo + 8 * k);
         const float4 cb = *reinterpret_cast<const float4*>(sCo + 8 * k + 4);
         co = Coef{ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
-      } else {
-        co = A.coef[k];
       }
       const f32x2 SIG = pk2(co.sig, co.sig), UA = pk2(co.ua, co.ua), UB = pk2(co.ub, co.ub);
       const f32x2 PA = pk2(co.pa, co.pa), PC = pk2(co.pc, co.pc), PB = pk2(co.pb, co.pb), TH = pk2(co.th, co.th);
@@ -358,8 +364,10 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
       // ---- u-step: pair e = 1 (holding the warp's last row) first
       {
         const float4 qb = *reinterpret_cast<const float4*>(sQ1 + (w + 1) * BW + j0);  // pbar1 of the row below
-        const ulonglong2 qn = *reinterpret_cast<const ulonglong2*>(myQL + 4);         // left edge of the lane to the right
-        const f32x2 QRn[2] = {l == 31 ? QR[0] : qn.x, l == 31 ? QR[1] : qn.y};
+        // left edge of the lane to the right; lane 31 reads the slot after it, which holds
+        // the tile's right side (0 when that side is on the image boundary)
+        const ulonglong2 qn = *reinterpret_cast<const ulonglong2*>(myQL + 4);
+        const f32x2 QRn[2] = {qn.x, qn.y};
         const float qbv[4] = {qb.x, qb.y, qb.z, qb.w};
 #pragma unroll
         for (int ee = 0; ee < 2; ++ee) {
@@ -368,9 +376,12 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
           for (int c = 0; c < 4; ++c) {
             const ulonglong2 fc = *reinterpret_cast<const ulonglong2*>(myF + c * 128);
             const f32x2 fg = e == 0 ? fc.x : fc.y;
-            const f32x2 below = e == 0 ? Q1[c][1] : pk2(hi2(Q1[c][0]), qbv[c]);
+            // bottom - top: for e = 1 the bottom rows (2, 4) straddle pair 0 and the row
+            // below, so the two lanes are subtracted as scalars straight into the pair
+            const f32x2 bt = e == 0 ? sub2(Q1[c][1], Q1[c][0])
+                                    : pk2(hi2(Q1[c][0]) - lo2(Q1[c][1]), qbv[c] - hi2(Q1[c][1]));
             const f32x2 right = c < 3 ? Q2[c + 1][e] : QRn[e];
-            const f32x2 d = sub2(add2(sub2(below, Q1[c][e]), right), Q2[c][e]);  // div_px
+            const f32x2 d = sub2(add2(bt, right), Q2[c][e]);  // div_px
             const f32x2 ub = fma2(SIG, d, U[c][e]);
             const bool dl = MASK && ((in_d >> (4 * c + e)) & 1u), dh = MASK && ((in_d >> (4 * c + e + 2)) & 1u);
             f32x2 un;
@@ -389,6 +400,9 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
         if (w < NW - 1)
           *reinterpret_cast<float4*>(sUB + (w + 1) * BW + j0) =
               make_float4(hi2(U[0][1]), hi2(U[1][1]), hi2(U[2][1]), hi2(U[3][1]));
+        else if (last_row_here && s_bot)  // the tile's last row, for the bottom side's update
+          *reinterpret_cast<float4*>(smem + L::XQH + j0) =
+              make_float4(hi2(U[0][1]), hi2(U[1][1]), hi2(U[2][1]), hi2(U[3][1]));
       }
       __syncthreads();
       if (need_uh) wait_u();  // u halo of iteration k
@@ -401,10 +415,12 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
         for (int e = 0; e < 2; ++e) {
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            const f32x2 above = e == 1 ? U[c][0] : pk2(uav[c], lo2(U[c][1]));
             const f32x2 leftu = c > 0 ? U[c - 1][e] : (e == 0 ? ul.x : ul.y);
             {
-              const f32x2 tt = fma2(PC, sub2(U[c][e], above), fma2(PA, P1[c][e], mul2(PB, H1[c][e])));  // p_target
+              // u - u_above: for e = 0 the rows above (-1, 1) straddle the halo and pair 1
+              const f32x2 du = e == 1 ? sub2(U[c][1], U[c][0])
+                                      : pk2(lo2(U[c][0]) - uav[c], hi2(U[c][0]) - lo2(U[c][1]));
+              const f32x2 tt = fma2(PC, du, fma2(PA, P1[c][e], mul2(PB, H1[c][e])));  // p_target
               const float l0 = e == 0 ? lim_top : 1.f;
               const f32x2 pn = pk2(fminf(fmaxf(lo2(tt), -l0), l0), fminf(fmaxf(hi2(tt), -1.f), 1.f));
               Q1[c][e] = fma2(TH, sub2(pn, P1[c][e]), pn);
@@ -426,25 +442,20 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
         }
         *reinterpret_cast<ulonglong2*>(myQL) = make_ulonglong2(Q2[0][0], Q2[0][1]);
       }
-      if (right_owner) {  // the right side's dofs, Du = -u of column 127 (pc (-u) = (-pc) u exactly)
-        const f32x2 NPC = pk2(-co.pc, -co.pc);
-        const ulonglong2 hrv = *reinterpret_cast<const ulonglong2*>(smem + L::HRS + 4 * w);
-        const f32x2 HR[2] = {hrv.x, hrv.y};
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const f32x2 tt = fma2(NPC, U[3][e], fma2(PA, PR[e], mul2(PB, HR[e])));
-          const f32x2 pn = pk2(fminf(fmaxf(lo2(tt), -1.f), 1.f), fminf(fmaxf(hi2(tt), -1.f), 1.f));
-          QR[e] = fma2(TH, sub2(pn, PR[e]), pn);
-          PR[e] = pn;
-        }
+      if (right_rows) {  // Du = -u of column 127 ((-pc) u = pc (-u) exactly)
+        const float tt = fmaf(-co.pc, smem[L::UR + r_slot], fmaf(co.pa, pr_s, co.pb * hr_s));
+        const float pn = fminf(fmaxf(tt, -1.f), 1.f);
+        smem[L::QL + r_slot] = fmaf(co.th, pn - pr_s, pn);
+        pr_s = pn;
       }
-      if (last_row_here && s_bot) {
+      if (bottom_warp && s_bot) {  // the tile's bottom side, Du = -u of the last row
         const float4 pv = *reinterpret_cast<const float4*>(smem + L::PBS + j0);
         const float4 hv = *reinterpret_cast<const float4*>(smem + L::HBS + j0);
+        const float4 uv = *reinterpret_cast<const float4*>(smem + L::XQH + j0);
         float pB[4] = {pv.x, pv.y, pv.z, pv.w}, qB[4];
-        const float hB[4] = {hv.x, hv.y, hv.z, hv.w};
+        const float hB[4] = {hv.x, hv.y, hv.z, hv.w}, uB[4] = {uv.x, uv.y, uv.z, uv.w};
 #pragma unroll
-        for (int c = 0; c < 4; ++c) p_update(pB[c], qB[c], -hi2(U[c][1]), hB[c], co);
+        for (int c = 0; c < 4; ++c) p_update(pB[c], qB[c], -uB[c], hB[c], co);
         *reinterpret_cast<float4*>(smem + L::PBS + j0) = make_float4(pB[0], pB[1], pB[2], pB[3]);
         *reinterpret_cast<float4*>(sQ1 + NW * BW + j0) = make_float4(qB[0], qB[1], qB[2], qB[3]);
       }
@@ -470,11 +481,11 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
 #pragma unroll
       for (int c = 0; c < 4; ++c) p2row[c] = lane4(P2[c][e], h);
       if (l == 0 && s_lft) A.out.SL[(size_t)(b - 1) * g.H + gi] = lane4(P2[0][e], h);
-      if (right_owner) {
-        const float pr = lane4(PR[e], h);
-        A.P2[(size_t)gi * W2 + c0 + 128 + b] = pr;
-        A.out.SR[(size_t)b * g.H + gi] = pr;
-      }
+    }
+    if (right_rows) {
+      const int gi = gb + l;
+      A.P2[(size_t)gi * W2 + c0 + 128 + b] = pr_s;
+      A.out.SR[(size_t)b * g.H + gi] = pr_s;
     }
     if (i0 == 0 && s_top)
       *reinterpret_cast<float4*>(A.out.ST + (ptrdiff_t)(a - 1) * g.W + c0 + j0) =
@@ -630,7 +641,9 @@ bool encode_maps(const LocalArgs& a, Mt4Maps* m) {
 
 bool fused_mt4_supported(const LocalArgs& a) {
   auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
-  return a.g.H == 128 * a.g.NR && a.g.W == 128 * a.g.NC && (a.g.W + a.g.NC) % 4 == 0 && al16(a.u) && al16(a.f) &&
+  // the inner loop reads every coefficient set from shared memory: K <= kMaxSmemCoef
+  return a.K <= Mt4Layout::kMaxSmemCoef && a.g.H == 128 * a.g.NR && a.g.W == 128 * a.g.NC &&
+         (a.g.W + a.g.NC) % 4 == 0 && al16(a.u) && al16(a.f) &&
          al16(a.P1) && al16(a.P2) && al16(a.lamh) && al16(a.lamv) && al16(a.out.ST) && al16(a.out.SB);
 }
 

@@ -115,13 +115,13 @@ def _batch_args(**over):
 
 
 @pytest.mark.parametrize("field,value,code,needle", [
-    ("height", 200, "EINVAL", "multiples of 128"),
-    ("width", 0, "EINVAL", "multiples of 128"),
+    ("height", 200, "EINVAL", "multiples of the subdomain side 128"),
+    ("width", 0, "EINVAL", "multiples of the subdomain side 128"),
     ("fidelity", 9, "EINVAL", "fidelity"),
     ("alpha", -2.0, "EINVAL", "alpha"),
     ("alpha", math.inf, "EINVAL", "alpha"),
     ("tau", 10.0, "EINVAL", "tau sigma"),          # tau given, sigma 0
-    ("tile", 64, "EUNSUPPORTED", "128"),
+    ("tile", 96, "EUNSUPPORTED", "64 or 128"),
     ("inner_iters", 0, "EINVAL", "inner_iters"),
     ("sigma0", 0.1, "EINVAL", "tau0 sigma0"),
     ("variant", 1, "EINVAL", "variant"),

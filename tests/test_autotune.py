@@ -64,14 +64,16 @@ def test_tuned_configuration_reaches_tolerance():
 
 
 def test_tune_batch_with_injected_measurement():
-    def fake(inner, variant, j_ref):
-        ms = {5: 30.0, 10: 25.0, 20: 32.0}[inner] + (5.0 if variant == 1 else 0.0)
-        return at.Trial(128, inner, variant, ms, 600 // inner, 8e-5, True)
+    """The batch autotuner searches subdomain side x K and keeps the fastest trial that
+    reached the tolerance."""
+    def fake(tile, inner, j_ref):
+        ms = {5: 30.0, 10: 25.0, 20: 32.0}[inner] + (5.0 if tile == 64 else 0.0)
+        return at.Trial(tile, inner, 0, ms, 600 // inner, 8e-5, True)
 
-    r = at.tune_batch([dict(height=128, width=128)], None, j_ref=[1.0], inners=(5, 10, 20), variants=(0, 1),
+    r = at.tune_batch([dict(height=128, width=128)], None, j_ref=[1.0], inners=(5, 10, 20), tiles=(64, 128),
                       solve_fn=fake)
-    assert (r.best.inner, r.best.variant) == (10, 0)
-    assert len(r.trials) == 6 and all(t.tile == 128 for t in r.trials)
+    assert (r.best.tile, r.best.inner) == (128, 10)
+    assert len(r.trials) == 6 and {t.tile for t in r.trials} == {64, 128}
 
 
 @pytest.mark.gpu
@@ -89,5 +91,6 @@ def test_tuned_batch_reaches_tolerance():
                         c1=0.2 if fid == "seg" else 0.0, c2=0.8 if fid == "seg" else 0.0, f=f))
     fs = [torch.from_numpy(m["f"]).cuda() for m in ims]
     jr = at.batch_reference_energies(ims, fs, inner=20, outer=1500)
-    r = at.tune_batch(ims, fs, tol=1e-3, j_ref=jr, inners=(5, 10), variants=(0,), max_outer=1500)
+    r = at.tune_batch(ims, fs, tol=1e-3, j_ref=jr, inners=(5, 10), tiles=(64, 128), max_outer=1500)
     assert r.best.reached and r.best.rel_err <= 1e-3
+    assert {t.tile for t in r.trials} == {64, 128} and all(t.reached for t in r.trials)

@@ -29,18 +29,19 @@ def _images():
     return out
 
 
-def test_batch_equals_single_image_solves_bitwise():
-    """The batch kernel (persistent clusters over the work list) gives each image the
-    bits of its own solve."""
+@pytest.mark.parametrize("tile", [128, 64])
+def test_batch_equals_single_image_solves_bitwise(tile):
+    """The batch kernels (128: persistent clusters over the work list; 64: one CTA per
+    subdomain) give each image the bits of its own solve."""
     L = _lib()
     ims = _images()
-    b = L.Batch(ims, inner_iters=10)
+    b = L.Batch(ims, inner_iters=10, tile=tile)
     fs = [torch.from_numpy(m["f"]).cuda() for m in ims]
     b.load(fs)
     b.iterate(13)
     for k, m in enumerate(ims):
         u_b = b.get_u(k, torch.empty_like(fs[k]))
-        p = L.make_params(m["height"], m["width"], m["height"] // 128, m["width"] // 128, fidelity=m["fidelity"],
+        p = L.make_params(m["height"], m["width"], m["height"] // tile, m["width"] // tile, fidelity=m["fidelity"],
                           alpha=m["alpha"], c1=m["c1"], c2=m["c2"], inner_iters=10)
         s = L.Solver(p)
         s.load(fs[k])
@@ -76,3 +77,22 @@ def test_batch_rejects_bad_shapes():
     with pytest.raises(L.DDTVError) as e:
         L.Batch([dict(height=100, width=128, fidelity="l2", alpha=1.0)])
     assert e.value.code == L.EINVAL
+
+
+def test_batch_graph_runs_compose():
+    """dd_tv_batch_iterate(n) is one graph launch of n outer iterations (captured per n
+    and start parity): 5 + 8 + 1 iterations give the bits of 14 in one call."""
+    L = _lib()
+    ims = _images()
+    fs = [torch.from_numpy(m["f"]).cuda() for m in ims]
+    outs = []
+    for runs in ((14,), (5, 8, 1)):
+        b = L.Batch(ims, inner_iters=10)
+        b.load(fs)
+        for n in runs:
+            b.iterate(n)
+        outs.append([b.get_u(k, torch.empty_like(fs[k])) for k in range(len(ims))])
+        b.close()
+    torch.cuda.synchronize()
+    for u1, u2 in zip(*outs):
+        assert torch.equal(u1, u2)

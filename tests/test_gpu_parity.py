@@ -296,8 +296,9 @@ def test_variant_count():
 def test_persistent_variants_bitwise_all_fidelities(fid, mask_prob, K):
     """The default 4 x 4 micro-tile mapping (tensor copies) against the cp.async 4 x 4
     (1), 2 x 4 micro-tile (2) and cluster-barrier (3) mappings for every fidelity, with
-    and without the inpainting mask, and with more inner iterations than the kernels
-    keep in shared memory (K = 70: coefficients 64.. come from global memory)."""
+    and without the inpainting mask, and with more inner iterations than the 4 x 4
+    kernel keeps coefficient sets in shared memory (K = 70 > 64: variants 0 and 1 then
+    run the 2 x 4 kernel, which reads the sets past 64 from global memory)."""
     L = _gpu()
     H, W = 384, 512  # 3 x 4 tiles: W + N_c = 516 keeps the p2 rows 16-byte aligned (variants 0, 1)
     f, _ = synth.rof_image(H, W, 12, 0.1, 5)
