@@ -46,7 +46,7 @@ WORKLOAD = "rof4096: ROF L2 denoising 4096x4096 fp32, alpha=8, 32x32 subdomains 
 SMEM_BYTES_PER_PX_ITER = 28  # minimum neighbour exchange per pixel per inner iteration
 JSTAR_FILE = os.path.join(ROOT, "tests", "golden", "jstar_rof4096_seed0.json")
 JSTAR_BATCH_FILE = os.path.join(ROOT, "tests", "golden", "jstar_batch64_seed0.json")
-PROFILE_FILE = os.path.join(ROOT, "profiles", "fused_local_rof4096.md")
+PROFILE_FILE = os.path.join(ROOT, "profiles", "fused_local_rof4096.json")
 
 
 def parse():
@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched multi-image measurement")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuned time-to-accuracy")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the unrolled-adjoint measurement")
+    ap.add_argument("--no-tvl1", action="store_true", help="skip the TV-L1 inpainting measurement")
     ap.add_argument("--replicas", action="store_true",
                     help="with --gpus N > 1: N independent replicas instead of one sharded image")
     return ap.parse_args()
@@ -173,22 +174,16 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def profile_traffic():
-    """(dram bytes per launch, sha) of the fused kernel from the committed ncu summary,
+def profile_data():
+    """The committed ncu figures of the fused kernel (profiles/fused_local_rof4096.json),
     or None when the kernel source changed since the capture."""
     if not os.path.exists(PROFILE_FILE):
         return None
-    vals = {}
-    for line in open(PROFILE_FILE):
-        if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
-            vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_sha256") != kernel_source_sha():
-        return None
     try:
-        return float(vals["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
+        rec = json.load(open(PROFILE_FILE))
+    except ValueError:
         return None
+    return rec if rec.get("kernel_source_sha256") == kernel_source_sha() else None
 
 
 def cpu_baseline(f, outer=2):
@@ -208,6 +203,77 @@ def cpu_baseline(f, outer=2):
     return {"value": H * W * INNER * outer / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{outer} outer iterations (x{INNER} inner) of the 4096^2 32x32-subdomain workload, "
                       f"FP64, OpenMP over subdomains, {dt:.1f} s"}
+
+
+def cpu_baseline_one_core(outer=1):
+    """The same oracle sample on one host core (OpenMP pinned to one thread in a child
+    process, so the parent's thread pool is untouched)."""
+    code = ("import sys, time, json, numpy as np; sys.path.insert(0, %r); import oracle, synth; "
+            "f, _ = synth.rof_image(%d, %d, %d, %r, %d); f = f.astype(np.float64); "
+            "pr = oracle.Problem(%d, %d, %d, %d, fidelity='l2', alpha=%r, inner=%d); "
+            "st = oracle.dd_init(pr, f); oracle.dd_run(pr, f, 0, state=st); t = time.perf_counter(); "
+            "oracle.dd_run(pr, f, %d, state=st); print(json.dumps(time.perf_counter() - t))"
+            % (ROOT, H, W, N_SHAPES, NOISE, SEED, H, W, NR, NC, ALPHA, INNER, outer))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr[-300:]}
+    dt = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": H * W * INNER * outer / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{outer} outer iteration (x{INNER} inner) of the 4096^2 workload on one core, {dt:.1f} s"}
+
+
+def measure_tvl1(dev, stream):
+    """TV-L1 inpainting + impulse denoising (2048^2, 10 % salt and pepper, Bernoulli(0.2)
+    mask, alpha 1.5, 16 x 16 subdomains of 128^2, K = 10), 500 outer iterations: device
+    throughput, the fused kernel's roofline, and the energy against the FP64 oracle at
+    equal iteration counts (20 outer iterations of both, from the same start)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+    from paper_1901_00682_gb300 import _lib as L
+    S, NT, OUT = 2048, 16, 500
+    f, mask, _ = synth.tvl1_inpaint_image(S, S, 100, 0.1, 0.2, 0)
+    fd = torch.from_numpy(f).to(dev)
+    md = torch.from_numpy(mask).to(dev)
+    p = L.make_params(S, S, NT, NT, fidelity="l1", alpha=1.5, inner_iters=INNER)
+    s = L.Solver(p, stream)
+    s.load(fd, md)
+    s.iterate(20)
+    J20 = s.current_energy()
+    s.load(fd, md)
+    s.iterate(OUT)                      # warm-up (graph capture)
+    s.load(fd, md)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.iterate(OUT)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    J500 = s.current_energy()
+    s.load(fd, md)
+    s.profile_read()
+    s.set_profiling(True)
+    s.iterate(40)
+    prof_ms, prof_n = s.profile_read()
+    s.set_profiling(False)
+    s.close()
+    local_ms = prof_ms["local"] / max(prof_n["local"], 1)
+    peak = L.measure_smem_bandwidth()
+    ach = SMEM_BYTES_PER_PX_ITER * S * S * INNER / (local_ms * 1e-3) / 1e9
+    pr = oracle.Problem(S, S, NT, NT, fidelity="l1", alpha=1.5, inner=INNER)
+    st = oracle.dd_run(pr, f.astype(np.float64), 20, mask=mask)
+    Jo = oracle.energy(pr, st.u, f.astype(np.float64), mask)
+    return {"workload": "tvl1_2048: TV-L1 inpainting + impulse denoising 2048x2048 fp32, 10% salt and pepper, "
+                        "Bernoulli(0.2) mask, alpha=1.5, 16x16 subdomains of 128x128, 10 inner/outer, 500 outer",
+            "ms_500_outer": ms, "value": S * S * INNER * OUT / (ms * 1e-3) / 1e6, "unit": UNIT,
+            "energy_500": J500,
+            "roofline": {"bound": "smem", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "avg_launch_ms": local_ms, "kernel": "k_fused_mt4t<L1, mask>"},
+            "energy_vs_oracle_20_outer": {"gpu": J20, "oracle": Jo, "rel_diff": abs(J20 - Jo) / abs(Jo)}}
 
 
 def measure_adjoint(dev):
@@ -325,8 +391,10 @@ def run_sharded(args, rank, world, local, dev, stream, pg):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for q in range(args.steps):
+        ss.solver.set_profiling(q % ENERGY_EVERY != 0)   # as in the single-GPU loop
         ss.step(1)
         if (q + 1) % ENERGY_EVERY == 0:
+            ss.solver.set_profiling(True)
             ss.energy()
     e1.record(stream)
     torch.cuda.synchronize(dev)
@@ -377,7 +445,7 @@ def run_sharded(args, rank, world, local, dev, stream, pg):
                        "parallelism": f"row-block shards x{world} (tile rows per rank: {NR}), cut strips exchanged "
                                       "by NCCL point-to-point every outer iteration, energy by float64 all-reduce",
                        "step": "1 outer iteration on every rank incl. the cut exchange, energy every 5 steps"},
-            "gpu_launches": int(sum(prof_n.values())) + row_tv}
+            "gpu_launches": 2 * args.steps + args.steps // ENERGY_EVERY + row_tv}
 
 
 def run_ours(args):
@@ -436,8 +504,13 @@ def run_ours(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for q in range(args.steps):
+        # per-phase CUDA events on every step except the first after a host read-back of
+        # the energy (there the stream runs dry and the bracket would include the host's
+        # submission of the next launches)
+        s.set_profiling(q % ENERGY_EVERY != 0)
         s.iterate(1)
         if (q + 1) % ENERGY_EVERY == 0:
+            s.set_profiling(True)
             s.current_energy()
     e1.record(stream)
     torch.cuda.synchronize(dev)
@@ -456,7 +529,8 @@ def run_ours(args):
     smem_peak = L.measure_smem_bandwidth()
     bytes_per_launch = SMEM_BYTES_PER_PX_ITER * H * W * INNER
     achieved = bytes_per_launch / (local_avg_ms * 1e-3) / 1e9
-    traffic = profile_traffic()
+    prof = profile_data()
+    traffic = prof.get("dram_bytes_per_launch") if prof else None
     iface_avg_ms = prof_ms["interface"] / max(prof_n["interface"], 1)
     energy_avg_ms = prof_ms["energy"] / max(prof_n["energy"], 1)
     n_if = 2 * (NR - 1) * W
@@ -472,6 +546,11 @@ def run_ours(args):
         "kernel": "fused local solver (k_fused_mt4t: persistent clusters of 8 CTAs x 128 threads, 3 CTAs per SM, one 128x128 subdomain per cluster at a time, 4x4 pixel micro-tile per thread, state moved by tensor copies)",
         "peak_source": "measured live: ld.shared probe kernel (dd_tv_measure_smem_bandwidth)",
         "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": local_avg_ms,
+        "occupancy": ({"achieved_warps_frac": prof.get("warps_active_frac"),
+                       "theoretical_warps_frac": prof.get("theoretical_warps_frac"),
+                       "ctas_per_sm": prof.get("ctas_per_sm"), "registers_per_thread": prof.get("registers"),
+                       "source": "ncu capture committed in profiles/fused_local_rof4096.json"}
+                      if prof else None),
         "hbm_state_stream": {"bytes_per_launch": 28 * H * W,
                              "achieved_gbs": 28 * H * W / (local_avg_ms * 1e-3) / 1e9,
                              "peak_gbs": hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
@@ -528,9 +607,37 @@ def run_ours(args):
                 dt = time.perf_counter() - t
                 tta[path] = {"ms": dt * 1e3, "device_ms": stt.ms, "outer_iters": stt.outer_done,
                              "rel_err": stt.rel_err, "reached": bool(stt.converged)}
+                if path != "fused":
+                    # one kernel per step streams the state through HBM: u-step 20 B/px (u
+                    # read and written, f, pbar1, pbar2), p-step 36 B/px (u; p1, p2 and their
+                    # proximal centres read; p1, p2, pbar1, pbar2 written)
+                    gbs = 56 * H * W * INNER * stt.outer_done / (stt.ms * 1e-3) / 1e9
+                    tta[path]["hbm"] = {"bytes_per_px_inner_iter": 56, "achieved_gbs": gbs, "peak_gbs": hbm_peak,
+                                        "frac": gbs / hbm_peak,
+                                        "note": "over the whole run, energy checks and multiplier updates included"}
                 sp.close()
             if tta["fused"]["reached"] and tta["plain"]["reached"]:
                 tta["speedup_vs_plain"] = tta["plain"]["ms"] / tta["fused"]["ms"]
+            if tta["fused"]["reached"]:
+                # m = infinity: the outer count the checked run stopped at, run without any
+                # energy evaluation (one graph replay), the tolerance checked after the fact
+                n_star = tta["fused"]["outer_iters"]
+                pt = L.make_params(H, W, NR, NC, fidelity="l2", alpha=ALPHA, inner_iters=INNER, path="fused")
+                sp = L.Solver(pt, stream)
+                sp.load(fd)
+                sp.iterate(n_star)          # warm-up (graph capture)
+                sp.load(fd)
+                torch.cuda.synchronize(dev)
+                t = time.perf_counter()
+                sp.iterate(n_star)
+                torch.cuda.synchronize(dev)
+                dt = time.perf_counter() - t
+                Jn = sp.current_energy()
+                sp.close()
+                tta["fused_no_checks"] = {"ms": dt * 1e3, "outer_iters": n_star,
+                                          "rel_err": (Jn - rec["J_star"]) / rec["J_star"],
+                                          "reached": (Jn - rec["J_star"]) / rec["J_star"] <= 1e-4,
+                                          "note": "m = infinity: energy evaluated once, after the timed run"}
             # adaptive inner stopping (eq. stop_inner1): the paper's tolerance and a loose
             # one, at most ADAPT_CAP inner iterations per local solve
             adaptive = {}
@@ -634,12 +741,19 @@ def run_ours(args):
     if not args.no_adjoint:
         adjoint = measure_adjoint(dev)
 
-    cpu = None
+    tvl1 = None
+    if not args.no_tvl1:
+        tvl1 = measure_tvl1(dev, stream)
+
+    cpu = cpu1 = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(f)
+        cpu1 = cpu_baseline_one_core()
 
     if rank == 0:
-        launches = int(sum(prof_n.values()))
+        # kernels of the timed region: per step the multiplier update and the local
+        # solves, per energy check the row-energy reduction
+        launches = 2 * args.steps + args.steps // ENERGY_EVERY
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -647,10 +761,12 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "l2": "state (~470 MB) larger than L2; no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "step": "1 outer iteration (interface + fused local solves), energy every 5 steps"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "time_to_accuracy": tta, "batch": batch,
-            "adjoint": adjoint,
+            "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_one_core": cpu1, "e2e": e2e,
+            "time_to_accuracy": tta, "batch": batch, "tvl1": tvl1, "adjoint": adjoint,
             "clocks": clocks.summary(), "gpu_launches": launches,
             "launches_by_phase": prof_n, "phase_ms": prof_ms,
+            "phase_note": "CUDA-event brackets of every phase launch in the timed steps except the first step "
+                          "after each energy read-back",
         }
         print(json.dumps(out), flush=True)
     s.close()

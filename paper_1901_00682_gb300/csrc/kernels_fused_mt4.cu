@@ -405,26 +405,21 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
               make_float4(hi2(U[0][1]), hi2(U[1][1]), hi2(U[2][1]), hi2(U[3][1]));
       }
       __syncthreads();
-      if (need_uh) wait_u();  // u halo of iteration k
-      // ---- p-step: pair e = 0 (holding the warp's first row) first
+      // ---- p-step: first the dofs that do not need the row above the warp (for warp 0
+      // that row is the u halo from the CTA above, which is still on its way), then the
+      // pbar1 of the warp's first row and its push upwards
       {
-        const float4 ua = *reinterpret_cast<const float4*>(sUB + w * BW + j0);  // u of the row above
         const ulonglong2 ul = *reinterpret_cast<const ulonglong2*>(myUR - 4);  // right column of the lane to the left
-        const float uav[4] = {ua.x, ua.y, ua.z, ua.w};
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             const f32x2 leftu = c > 0 ? U[c - 1][e] : (e == 0 ? ul.x : ul.y);
-            {
-              // u - u_above: for e = 0 the rows above (-1, 1) straddle the halo and pair 1
-              const f32x2 du = e == 1 ? sub2(U[c][1], U[c][0])
-                                      : pk2(lo2(U[c][0]) - uav[c], hi2(U[c][0]) - lo2(U[c][1]));
-              const f32x2 tt = fma2(PC, du, fma2(PA, P1[c][e], mul2(PB, H1[c][e])));  // p_target
-              const float l0 = e == 0 ? lim_top : 1.f;
-              const f32x2 pn = pk2(fminf(fmaxf(lo2(tt), -l0), l0), fminf(fmaxf(hi2(tt), -1.f), 1.f));
-              Q1[c][e] = fma2(TH, sub2(pn, P1[c][e]), pn);
-              P1[c][e] = pn;
+            if (e == 1) {
+              const f32x2 tt = fma2(PC, sub2(U[c][1], U[c][0]), fma2(PA, P1[c][1], mul2(PB, H1[c][1])));  // p_target
+              const f32x2 pn = pk2(fminf(fmaxf(lo2(tt), -1.f), 1.f), fminf(fmaxf(hi2(tt), -1.f), 1.f));
+              Q1[c][1] = fma2(TH, sub2(pn, P1[c][1]), pn);
+              P1[c][1] = pn;
             }
             {
               const f32x2 tt = fma2(PC, sub2(U[c][e], leftu), fma2(PA, P2[c][e], mul2(PB, H2[c][e])));
@@ -434,13 +429,23 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
               P2[c][e] = pn;
             }
           }
-          if (e == 0) {
-            const float4 q = make_float4(lo2(Q1[0][0]), lo2(Q1[1][0]), lo2(Q1[2][0]), lo2(Q1[3][0]));
-            if (w > 0) *reinterpret_cast<float4*>(sQ1 + w * BW + j0) = q;
-            if (push_up) st_async_v4_f32(remote_q1, q.x, q.y, q.z, q.w, remote_mbQ);
-          }
         }
         *reinterpret_cast<ulonglong2*>(myQL) = make_ulonglong2(Q2[0][0], Q2[0][1]);
+        if (need_uh) wait_u();  // u halo of iteration k
+        const float4 ua = *reinterpret_cast<const float4*>(sUB + w * BW + j0);  // u of the row above
+        const float uav[4] = {ua.x, ua.y, ua.z, ua.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          // u - u_above of rows (0, 2): the rows above (-1, 1) straddle the halo and pair 1
+          const f32x2 du = pk2(lo2(U[c][0]) - uav[c], hi2(U[c][0]) - lo2(U[c][1]));
+          const f32x2 tt = fma2(PC, du, fma2(PA, P1[c][0], mul2(PB, H1[c][0])));
+          const f32x2 pn = pk2(fminf(fmaxf(lo2(tt), -lim_top), lim_top), fminf(fmaxf(hi2(tt), -1.f), 1.f));
+          Q1[c][0] = fma2(TH, sub2(pn, P1[c][0]), pn);
+          P1[c][0] = pn;
+        }
+        const float4 q = make_float4(lo2(Q1[0][0]), lo2(Q1[1][0]), lo2(Q1[2][0]), lo2(Q1[3][0]));
+        if (w > 0) *reinterpret_cast<float4*>(sQ1 + w * BW + j0) = q;
+        if (push_up) st_async_v4_f32(remote_q1, q.x, q.y, q.z, q.w, remote_mbQ);
       }
       if (right_rows) {  // Du = -u of column 127 ((-pc) u = pc (-u) exactly)
         const float tt = fmaf(-co.pc, smem[L::UR + r_slot], fmaf(co.pa, pr_s, co.pb * hr_s));
