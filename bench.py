@@ -543,6 +543,9 @@ def run_ours(args):
     roofline = {
         "bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s", "frac": achieved / smem_peak,
         "traffic": traffic,
+        "traffic_note": ("DRAM bytes per launch from the committed ncu capture; the bound is shared memory, "
+                         "the HBM state stream is hbm_state_stream below (writes still in L2 at kernel exit "
+                         "are not counted by ncu)") if traffic else None,
         "kernel": "fused local solver (k_fused_mt4t: persistent clusters of 8 CTAs x 128 threads, 3 CTAs per SM, one 128x128 subdomain per cluster at a time, 4x4 pixel micro-tile per thread, state moved by tensor copies)",
         "peak_source": "measured live: ld.shared probe kernel (dd_tv_measure_smem_bandwidth)",
         "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": local_avg_ms,
