@@ -79,7 +79,7 @@ __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.w
 // p_update with the clamp to [-lim, lim]; lim = 0 pins an inactive dof at 0
 __device__ __forceinline__ void p_update_lim(float& p, float& pbar, float du, float phat, const Coef& c, float lim) {
   const float t = p_target(p, du, phat, c);
-  const float pn = fminf(fmaxf(t, -lim), lim);
+  const float pn = clamp_abs(t, lim);
   pbar = fmaf(c.th, pn - p, pn);
   p = pn;
 }

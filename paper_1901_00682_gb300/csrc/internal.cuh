@@ -136,7 +136,9 @@ cudaError_t launch_fused_mt_batch(const BatchArgs& B, int total_tiles, cudaStrea
 // (fused_mt4_supported).
 bool fused_mt4_supported(const LocalArgs& a);
 // tma: move the state with tensor copies (falls back to cp.async if the tensor maps
-// cannot be encoded)
+// cannot be encoded).  With a.inner_tol2 > 0 (adaptive inner stop) the tensor-copy
+// kernel runs whatever tma says, and cudaErrorNotSupported comes back if its maps
+// cannot be encoded.
 cudaError_t launch_fused_mt4(const LocalArgs& a, int fidelity, bool tma, cudaStream_t st);
 cudaError_t fused_mt4_prepare();
 

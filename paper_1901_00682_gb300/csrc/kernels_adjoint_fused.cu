@@ -49,7 +49,7 @@ __device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.a
 // fused forward kernel; returns the projection's pass bit (0 for an inactive dof).
 __device__ __forceinline__ uint32_t p_step_bit(float& p, float& pbar, float du, float phat, const Coef& c, float lim) {
   const float t = p_target(p, du, phat, c);
-  const float pn = fminf(fmaxf(t, -lim), lim);
+  const float pn = clamp_abs(t, lim);
   pbar = fmaf(c.th, pn - p, pn);
   p = pn;
   return (lim > 0.f && t >= -1.0f && t <= 1.0f) ? 1u : 0u;

@@ -480,7 +480,13 @@ cudaError_t launch_fused_batch(const BatchArgs& B, int total_tiles, int tile, cu
 cudaError_t launch_fused_local(const LocalArgs& a, int fid, int variant, cudaStream_t st) {
   // largest tile of the (ragged) partition
   const int mr = (a.g.H + a.g.NR - 1) / a.g.NR, mc = (a.g.W + a.g.NC - 1) / a.g.NC;
-  if (a.inner_tol2 <= 0.0 && a.g.H == 128 * a.g.NR && a.g.W == 128 * a.g.NC) {  // every tile exactly 128 x 128
+  const bool exact128 = a.g.H == 128 * a.g.NR && a.g.W == 128 * a.g.NC;  // every tile exactly 128 x 128
+  if (a.inner_tol2 > 0.0 && exact128 && variant == 0 && fused_mt4_supported(a)) {
+    // adaptive inner stop in the default kernel (the other variants: the cluster-barrier kernel)
+    const cudaError_t e = launch_fused_mt4(a, fid, true, st);
+    if (e != cudaErrorNotSupported) return e;
+  }
+  if (a.inner_tol2 <= 0.0 && exact128) {
     switch (variant) {
       case 0:  // default: persistent 4 x 4 micro-tiles, tensor copies
       case 1:  // the same with cp.async copies

@@ -356,14 +356,14 @@ __device__ __forceinline__ void fused_mt_body(const LocalArgs& A, const int firs
             {
               const f32x2 tt = fma2(PC, sub2(U[c][e], above), fma2(PA, P1[c][e], mul2(PB, H1[c][e])));  // p_target
               const float l0 = e == 0 ? lim_top : 1.f;
-              const f32x2 pn = pk2(fminf(fmaxf(lo2(tt), -l0), l0), fminf(fmaxf(hi2(tt), -1.f), 1.f));
+              const f32x2 pn = pk2(clamp_abs(lo2(tt), l0), clamp_abs(hi2(tt), 1.f));
               Q1[c][e] = fma2(TH, sub2(pn, P1[c][e]), pn);
               P1[c][e] = pn;
             }
             {
               const f32x2 tt = fma2(PC, sub2(U[c][e], leftu), fma2(PA, P2[c][e], mul2(PB, H2[c][e])));
               const float l = c == 0 ? lim_left : 1.f;
-              const f32x2 pn = pk2(fminf(fmaxf(lo2(tt), -l), l), fminf(fmaxf(hi2(tt), -l), l));
+              const f32x2 pn = pk2(clamp_abs(lo2(tt), l), clamp_abs(hi2(tt), l));
               Q2[c][e] = fma2(TH, sub2(pn, P2[c][e]), pn);
               P2[c][e] = pn;
             }
@@ -734,14 +734,14 @@ __device__ __forceinline__ void fused_mt_run(const Src& S, const int first, cons
             {
               const f32x2 tt = fma2(PC, sub2(U[c][e], above), fma2(PA, P1[c][e], mul2(PB, H1[c][e])));  // p_target
               const float l0 = e == 0 ? lim_top : 1.f;
-              const f32x2 pn = pk2(fminf(fmaxf(lo2(tt), -l0), l0), fminf(fmaxf(hi2(tt), -1.f), 1.f));
+              const f32x2 pn = pk2(clamp_abs(lo2(tt), l0), clamp_abs(hi2(tt), 1.f));
               Q1[c][e] = fma2(TH, sub2(pn, P1[c][e]), pn);
               P1[c][e] = pn;
             }
             {
               const f32x2 tt = fma2(PC, sub2(U[c][e], leftu), fma2(PA, P2[c][e], mul2(PB, H2[c][e])));
               const float l = c == 0 ? lim_left : 1.f;
-              const f32x2 pn = pk2(fminf(fmaxf(lo2(tt), -l), l), fminf(fmaxf(hi2(tt), -l), l));
+              const f32x2 pn = pk2(clamp_abs(lo2(tt), l), clamp_abs(hi2(tt), l));
               Q2[c][e] = fma2(TH, sub2(pn, P2[c][e]), pn);
               P2[c][e] = pn;
             }

@@ -8,8 +8,8 @@
 // neighbours never leaves the warp.  A CTA is four warps (128 threads) covering a band
 // of 16 rows; with up to 170 registers per thread three CTAs fit on an SM, which then
 // interleaves three subdomain bands instead of two.  The tile's right side (the p2 dofs
-// of column 128) belongs to lane 31 (the holder of column 127), in registers; the
-// bottom side to the last warp of the last CTA.
+// of column 128) is updated by lanes 0..15 of warp 1, one band row each, in registers;
+// the bottom side by warp 2 of the last CTA.
 //
 // Per inner iteration a lane exchanges, with one 16-byte shared-memory access each, the
 // u of its right column (for the lane to its right), the pbar2 of its left edge (for
@@ -29,6 +29,20 @@
 // (bulk group, issued after the barrier that follows the out-buffer writes; the buffer
 // is rewritten only after a wait for the copies to have read it); p2 and the sides go
 // out with ordinary stores.
+//
+// ADAPT (tensor-copy kernel only): adaptive inner stopping (Section 5, eq. stop_inner1).
+// Every thread sums (p^{k+1} - p^k)^2 and (p^{k+1})^2 over its dofs in the p-step of
+// iteration k (packed float32 pairs) and leaves them in the P1 out-buffer, idle during
+// the inner loop.  At the start of iteration k + 1 one warp adds the CTA's 128 pairs
+// (float32, fixed order) and sends the CTA's pair with st.async to slot `rank` of every
+// CTA of the cluster, counted on one of two mbarriers (by the parity of the phase, so
+// that a phase is always consumed everywhere before its barrier is armed again).  Before
+// the barrier between the u-step and the p-step of iteration k + 1, one warp per CTA
+// waits for the CL pairs and adds them in a fixed tree: every CTA takes the same
+// decision without a cluster barrier.  On "stop" the u-step of iteration k + 1 is undone
+// (each iteration first copies u into the u out-buffer, which then already holds the
+// result), its u halo is drained and the p-step is skipped: the solve keeps k + 1 inner
+// iterations, as the rule prescribes.
 #include <cuda.h>
 
 #include "fused_common.cuh"
@@ -71,8 +85,23 @@ struct Mt4Layout {
   // tensor-copy variant: out-buffers of u and p1 (128-byte aligned), three mbarriers
   static constexpr int OU = (HBS + BW + 31) & ~31;
   static constexpr int OP1 = OU + BAND * BW;
-  static constexpr int MBT = OP1 + BAND * BW;
-  static constexpr size_t BYTES_TMA = sizeof(float) * MBT + 32;
+  // adaptive inner stop: during the inner loop OP1 holds every thread's residual sums (4
+  // floats per thread); two buffers (one per parity of the reduction phase) of CL
+  // slots, one (sum (dp)^2, sum p^2) pair per CTA of the cluster; the CTA's decision
+  static constexpr int PS = OP1;
+  static constexpr int RED = OP1 + BAND * BW;
+  static constexpr uint32_t kRedBytes = 8 * CL;  // one phase: every CTA's pair
+  static constexpr int STOP = RED + 2 * 2 * CL;
+  static constexpr int MBT = STOP + 2;           // five mbarriers
+#ifndef MT4_REDUCE_WARP
+#define MT4_REDUCE_WARP 3
+#endif
+#ifndef MT4_DECIDE_WARP
+#define MT4_DECIDE_WARP 1
+#endif
+  static constexpr int kReduceWarp = MT4_REDUCE_WARP;  // adds the CTA's residual sums and sends them
+  static constexpr int kDecideWarp = MT4_DECIDE_WARP;  // takes the stop decision
+  static constexpr size_t BYTES_TMA = sizeof(float) * MBT + 48;
   static constexpr uint32_t kTmaBytes = 4 * (3 * BAND * BW + BAND * P2S);  // one subdomain's four tensor loads
   static_assert(Q1 % 4 == 0 && UR % 4 == 0 && QL % 4 == 0 && F % 4 == 0 && CO % 4 == 0 && SU % 4 == 0 &&
                     SP2 % 4 == 0 && XLT % 4 == 0 && XLL % 4 == 0 && XLR % 4 == 0 && PBS % 4 == 0 &&
@@ -81,6 +110,8 @@ struct Mt4Layout {
   static_assert(CL * BAND == 128, "a cluster of CTAs covers the 128 rows of a tile");
   static_assert(SU % 32 == 0 && SP2 % 32 == 0 && (BAND * BW) % 32 == 0 && OU % 32 == 0 && OP1 % 32 == 0,
                 "tensor copies need 128-byte aligned shared memory");
+  static_assert(RED % 2 == 0 && MBT % 2 == 0, "8-byte alignment of the reduction slots and mbarriers");
+  static_assert(4 * NT <= BAND * BW, "the residual sums of every thread fit the P1 out-buffer");
 };
 
 // tensor maps of the state arrays: u, f, p1 with 128 x 16 boxes, p2 with 132 x 16 boxes
@@ -108,7 +139,7 @@ __device__ __forceinline__ void tma_fence_smem() { asm volatile("fence.proxy.asy
 
 __device__ __forceinline__ float lane4(f32x2 v, int h) { return h ? hi2(v) : lo2(v); }
 
-template <int FID, bool MASK, bool TMA>
+template <int FID, bool MASK, bool TMA, bool ADAPT>
 __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps* M, const int first,
                                                const int stride) {
   using L = Mt4Layout;
@@ -120,6 +151,8 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
   const uint32_t mbU = smem_addr(smem + (TMA ? L::MBT : L::MB));
   const uint32_t mbQ = mbU + 8;
   const uint32_t mbL = mbU + 16;  // tensor loads of the staged subdomain (TMA)
+  const uint32_t mbR = mbU + 24;  // reduction phases of the adaptive stop, two mbarriers (parity)
+  static_assert(!ADAPT || TMA, "the adaptive stop keeps the rolled-back u in the tensor-copy out-buffer");
 
   const Grid g = A.g;
   const int T = g.NR * g.NC;
@@ -157,6 +190,10 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
     mbar_init(mbU, 1);
     mbar_init(mbQ, 1);
     if (TMA) mbar_init(mbL, 1);
+    if (ADAPT) {
+      mbar_init(mbR, 1);
+      mbar_init(mbR + 8, 1);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int q = tid; q < 8 * K; q += NT) sCo[q] = reinterpret_cast<const float*>(A.coef)[q];  // K <= kMaxSmemCoef
@@ -165,6 +202,10 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
   __syncthreads();
   if (need_uh && l == 0) mbar_arrive_expect_tx(mbU, kHaloBytes);
   if (need_qh && l == 0) mbar_arrive_expect_tx(mbQ, kHaloBytes);
+  if (ADAPT && tid == 32 * L::kDecideWarp) {  // lane 0 of the deciding warp arms both reduction barriers
+    mbar_arrive_expect_tx(mbR, L::kRedBytes);
+    mbar_arrive_expect_tx(mbR + 8, L::kRedBytes);
+  }
   cluster_arrive<true>();  // barriers initialised and armed everywhere before any halo is sent
   cluster_wait();
 
@@ -234,6 +275,7 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
   if (first < T) prefetch(first);
   uint32_t nsub = 0;             // subdomains started (phase of mbL)
   int pa = -1, pc0 = 0, pgb = 0;  // previous subdomain, whose u and p1 wait in the out-buffer (TMA)
+  uint32_t gred = 0;              // adaptive stop: reduction phases sent (and consumed) so far
 
   for (int t = first; t < T; t += stride, ++nsub) {
     const int a = t / g.NC, b = t - a * g.NC;
@@ -254,6 +296,7 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
     // pairs [column c][e]: rows (e, e + 2) of column j0 + c
     f32x2 U[4][2], P1[4][2], P2[4][2], H1[4][2], H2[4][2], Q1[4][2], Q2[4][2];
     uint32_t in_d = 0;  // bit 4c + r: pixel (row r, column j0 + c) lies in the inpainting domain
+    int k_run = K;  // adaptive stop: inner iterations kept (< K: u of the last u-step undone)
 
     cp_async_wait_all();
     if (TMA && !mbar_wait(mbL, nsub & 1)) timed_out = true;
@@ -360,6 +403,40 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
       }
       const f32x2 SIG = pk2(co.sig, co.sig), UA = pk2(co.ua, co.ua), UB = pk2(co.ub, co.ub);
       const f32x2 PA = pk2(co.pa, co.pa), PC = pk2(co.pc, co.pc), PB = pk2(co.pb, co.pb), TH = pk2(co.th, co.th);
+      // adaptive stop: this thread's sums of (p^{k+1} - p^k)^2 and (p^{k+1})^2 over its dofs
+      f32x2 AD = 0ull, AP = 0ull;
+      auto res2 = [&](f32x2 pn, f32x2 po) {
+        const f32x2 d = sub2(pn, po);
+        AD = fma2(d, d, AD);
+        AP = fma2(pn, pn, AP);
+      };
+      if (ADAPT && k > 0) {
+        // u of iteration k - 1 into the out-buffer: the result if the decision on iteration
+        // k - 1, taken during this u-step, stops the solve
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int e = r & 1, h = r >> 1;
+          *reinterpret_cast<float4*>(smem + L::OU + (lr0 + r) * BW + j0) =
+              make_float4(lane4(U[0][e], h), lane4(U[1][e], h), lane4(U[2][e], h), lane4(U[3][e], h));
+        }
+      }
+      if (ADAPT && k > 0 && w == L::kReduceWarp) {
+        // the CTA's residual sums of iteration k - 1 to every CTA of the cluster (this warp
+        // then waits for the pbar1 halo anyway)
+        f32x2 D = 0ull, P = 0ull;
+#pragma unroll
+        for (int q = 0; q < NT / 32; ++q) {
+          const float4 r = *reinterpret_cast<const float4*>(smem + L::PS + 4 * (l + 32 * q));
+          D = add2(D, pk2(r.x, r.y));
+          P = add2(P, pk2(r.z, r.w));
+        }
+        f32x2 v = pk2(lo2(D) + hi2(D), lo2(P) + hi2(P));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = add2(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (l < CL)  // lane l to CTA l, slot rank
+          st_async_v2(map_rank(smem_addr(smem + L::RED + 2 * CL * (gred & 1) + 2 * rank), l), lo2(v), hi2(v),
+                      map_rank(mbR + 8 * (gred & 1), l));
+      }
       if (need_qh && k > 0) wait_q();  // pbar1 halo of iteration k-1
       // ---- u-step: pair e = 1 (holding the warp's last row) first
       {
@@ -404,7 +481,34 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
           *reinterpret_cast<float4*>(smem + L::XQH + j0) =
               make_float4(hi2(U[0][1]), hi2(U[1][1]), hi2(U[2][1]), hi2(U[3][1]));
       }
+      // adaptive stop: the P1 out-buffer takes the residual sums of this iteration's p-step
+      if (ADAPT && k == 0 && tid == 0) tma_wait_read();
+      if (ADAPT && k > 0) {
+        // decision on iteration k - 1 (eq. stop_inner1): the deciding warp adds the CL CTA
+        // pairs in a fixed tree, so every CTA of the cluster takes the same decision
+        if (w == L::kDecideWarp) {
+          const uint32_t mb = mbR + 8 * (gred & 1);
+          if (!mbar_wait(mb, (gred >> 1) & 1)) timed_out = true;
+          f32x2 v = l < CL ? *reinterpret_cast<const f32x2*>(smem + L::RED + 2 * CL * (gred & 1) + 2 * l) : 0ull;
+#pragma unroll
+          for (int o = CL / 2; o > 0; o >>= 1) v = add2(v, __shfl_xor_sync(0xffffffffu, v, o));
+          if (l == 0) {
+            mbar_arrive_expect_tx(mb, L::kRedBytes);  // the barrier's next phase
+            const float td = lo2(v), tp = hi2(v);
+            *reinterpret_cast<int*>(smem + L::STOP) =
+                (timed_out || tp == 0.f || td < (float)A.inner_tol2 * tp) ? 1 : 0;
+          }
+        }
+        ++gred;
+      }
       __syncthreads();
+      if (ADAPT && k > 0 && *reinterpret_cast<const int*>(smem + L::STOP)) {
+        // keep iterations 0 .. k - 1: u of iteration k - 1 waits in the out-buffer; the u
+        // halo this u-step sent is drained
+        k_run = k;
+        if (need_uh) wait_u();
+        break;
+      }
       // ---- p-step: first the dofs that do not need the row above the warp (for warp 0
       // that row is the u halo from the CTA above, which is still on its way), then the
       // pbar1 of the warp's first row and its push upwards
@@ -417,15 +521,17 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
             const f32x2 leftu = c > 0 ? U[c - 1][e] : (e == 0 ? ul.x : ul.y);
             if (e == 1) {
               const f32x2 tt = fma2(PC, sub2(U[c][1], U[c][0]), fma2(PA, P1[c][1], mul2(PB, H1[c][1])));  // p_target
-              const f32x2 pn = pk2(fminf(fmaxf(lo2(tt), -1.f), 1.f), fminf(fmaxf(hi2(tt), -1.f), 1.f));
+              const f32x2 pn = pk2(clamp_abs(lo2(tt), 1.f), clamp_abs(hi2(tt), 1.f));
               Q1[c][1] = fma2(TH, sub2(pn, P1[c][1]), pn);
+              if (ADAPT) res2(pn, P1[c][1]);
               P1[c][1] = pn;
             }
             {
               const f32x2 tt = fma2(PC, sub2(U[c][e], leftu), fma2(PA, P2[c][e], mul2(PB, H2[c][e])));
               const float ll = c == 0 ? lim_left : 1.f;
-              const f32x2 pn = pk2(fminf(fmaxf(lo2(tt), -ll), ll), fminf(fmaxf(hi2(tt), -ll), ll));
+              const f32x2 pn = pk2(clamp_abs(lo2(tt), ll), clamp_abs(hi2(tt), ll));
               Q2[c][e] = fma2(TH, sub2(pn, P2[c][e]), pn);
+              if (ADAPT) res2(pn, P2[c][e]);
               P2[c][e] = pn;
             }
           }
@@ -439,8 +545,9 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
           // u - u_above of rows (0, 2): the rows above (-1, 1) straddle the halo and pair 1
           const f32x2 du = pk2(lo2(U[c][0]) - uav[c], hi2(U[c][0]) - lo2(U[c][1]));
           const f32x2 tt = fma2(PC, du, fma2(PA, P1[c][0], mul2(PB, H1[c][0])));
-          const f32x2 pn = pk2(fminf(fmaxf(lo2(tt), -lim_top), lim_top), fminf(fmaxf(hi2(tt), -1.f), 1.f));
+          const f32x2 pn = pk2(clamp_abs(lo2(tt), lim_top), clamp_abs(hi2(tt), 1.f));
           Q1[c][0] = fma2(TH, sub2(pn, P1[c][0]), pn);
+          if (ADAPT) res2(pn, P1[c][0]);
           P1[c][0] = pn;
         }
         const float4 q = make_float4(lo2(Q1[0][0]), lo2(Q1[1][0]), lo2(Q1[2][0]), lo2(Q1[3][0]));
@@ -449,8 +556,9 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
       }
       if (right_rows) {  // Du = -u of column 127 ((-pc) u = pc (-u) exactly)
         const float tt = fmaf(-co.pc, smem[L::UR + r_slot], fmaf(co.pa, pr_s, co.pb * hr_s));
-        const float pn = fminf(fmaxf(tt, -1.f), 1.f);
+        const float pn = clamp_abs(tt, 1.f);
         smem[L::QL + r_slot] = fmaf(co.th, pn - pr_s, pn);
+        if (ADAPT) res2(pk2(pn, 0.f), pk2(pr_s, 0.f));
         pr_s = pn;
       }
       if (bottom_warp && s_bot) {  // the tile's bottom side, Du = -u of the last row
@@ -460,14 +568,26 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
         float pB[4] = {pv.x, pv.y, pv.z, pv.w}, qB[4];
         const float hB[4] = {hv.x, hv.y, hv.z, hv.w}, uB[4] = {uv.x, uv.y, uv.z, uv.w};
 #pragma unroll
-        for (int c = 0; c < 4; ++c) p_update(pB[c], qB[c], -uB[c], hB[c], co);
+        for (int c = 0; c < 4; ++c) {
+          const float po = pB[c];
+          p_update(pB[c], qB[c], -uB[c], hB[c], co);
+          if (ADAPT) res2(pk2(pB[c], 0.f), pk2(po, 0.f));
+        }
         *reinterpret_cast<float4*>(smem + L::PBS + j0) = make_float4(pB[0], pB[1], pB[2], pB[3]);
         *reinterpret_cast<float4*>(sQ1 + NW * BW + j0) = make_float4(qB[0], qB[1], qB[2], qB[3]);
       }
-      if (TMA && k == K - 1 && tid == 0) tma_wait_read();  // the out-buffer is free for this subdomain's bands
+      if (ADAPT && k + 1 < K)  // this thread's residual sums, added up at the start of iteration k + 1
+        *reinterpret_cast<float4*>(smem + L::PS + 4 * tid) = make_float4(lo2(AD), hi2(AD), lo2(AP), hi2(AP));
+      if (!ADAPT && TMA && k == K - 1 && tid == 0) tma_wait_read();  // the out-buffer is free for this subdomain's bands
       __syncthreads();
     }
-    if (need_qh) wait_q();  // drain the last pbar1 halo (not read)
+    const bool stopped = ADAPT && k_run < K;
+    if (need_qh && !stopped) wait_q();  // drain the last pbar1 halo (not read)
+    if (ADAPT && rank == 0 && tid == 0) {
+      A.inner_used[t] = k_run;
+      atomicMax(A.inner_max, k_run);
+      atomicAdd(A.inner_work, (unsigned long long)(BW * BW) * (unsigned long long)k_run);
+    }
 
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -476,7 +596,7 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
       const float4 uv = make_float4(lane4(U[0][e], h), lane4(U[1][e], h), lane4(U[2][e], h), lane4(U[3][e], h));
       const float4 pv = make_float4(lane4(P1[0][e], h), lane4(P1[1][e], h), lane4(P1[2][e], h), lane4(P1[3][e], h));
       if (TMA) {
-        *reinterpret_cast<float4*>(smem + L::OU + (lr0 + r) * BW + j0) = uv;
+        if (!stopped) *reinterpret_cast<float4*>(smem + L::OU + (lr0 + r) * BW + j0) = uv;
         *reinterpret_cast<float4*>(smem + L::OP1 + (lr0 + r) * BW + j0) = pv;
       } else {
         *reinterpret_cast<float4*>(A.u + (size_t)gi * g.W + c0 + j0) = uv;
@@ -524,18 +644,21 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
 
 template <int FID, bool MASK>
 __global__ void __launch_bounds__(Mt4Layout::NT, 3) k_fused_mt4(const LocalArgs A) {
-  fused_mt4_body<FID, MASK, false>(A, nullptr, blockIdx.y, gridDim.y);
+  fused_mt4_body<FID, MASK, false, false>(A, nullptr, blockIdx.y, gridDim.y);
 }
 
-template <int FID, bool MASK>
+template <int FID, bool MASK, bool ADAPT>
 __global__ void __launch_bounds__(Mt4Layout::NT, 3) k_fused_mt4t(const LocalArgs A, const __grid_constant__ Mt4Maps M) {
-  fused_mt4_body<FID, MASK, true>(A, &M, blockIdx.y, gridDim.y);
+  fused_mt4_body<FID, MASK, true, ADAPT>(A, &M, blockIdx.y, gridDim.y);
 }
 
-// clusters of each kernel resident at once, per device: [TMA][FID * 2 + MASK]
-int& mt4_clusters(int dev, bool tma, int fid, bool mask) {
-  static int n[64][2][6] = {};
-  return n[dev & 63][tma ? 1 : 0][fid * 2 + (mask ? 1 : 0)];
+// kernel kinds: cp.async copies, tensor copies, tensor copies with the adaptive stop
+enum Mt4Kind { kMt4Cp = 0, kMt4Tma = 1, kMt4TmaAdapt = 2 };
+
+// clusters of each kernel resident at once, per device: [kind][FID * 2 + MASK]
+int& mt4_clusters(int dev, int kind, int fid, bool mask) {
+  static int n[64][3][6] = {};
+  return n[dev & 63][kind][fid * 2 + (mask ? 1 : 0)];
 }
 
 cudaLaunchConfig_t mt4_config(int clusters, bool tma, cudaLaunchAttribute* attr) {
@@ -553,7 +676,8 @@ cudaLaunchConfig_t mt4_config(int clusters, bool tma, cudaLaunchAttribute* attr)
 }
 
 template <class Kern>
-cudaError_t prepare_kernel(Kern kern, bool tma, int fid, bool mask) {
+cudaError_t prepare_kernel(Kern kern, int kind, int fid, bool mask) {
+  const bool tma = kind != kMt4Cp;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(tma ? Mt4Layout::BYTES_TMA : Mt4Layout::BYTES));
   if (e != cudaSuccess) return e;
@@ -566,39 +690,52 @@ cudaError_t prepare_kernel(Kern kern, bool tma, int fid, bool mask) {
   }
   int dev = 0;
   cudaGetDevice(&dev);
-  mt4_clusters(dev, tma, fid, mask) = n;
+  mt4_clusters(dev, kind, fid, mask) = n;
   return cudaSuccess;
 }
 
 template <int FID, bool MASK>
 cudaError_t prepare_mt4_one() {
-  cudaError_t e = prepare_kernel(k_fused_mt4<FID, MASK>, false, FID, MASK);
+  cudaError_t e = prepare_kernel(k_fused_mt4<FID, MASK>, kMt4Cp, FID, MASK);
   if (e != cudaSuccess) return e;
-  return prepare_kernel(k_fused_mt4t<FID, MASK>, true, FID, MASK);
+  if ((e = prepare_kernel(k_fused_mt4t<FID, MASK, false>, kMt4Tma, FID, MASK)) != cudaSuccess) return e;
+  return prepare_kernel(k_fused_mt4t<FID, MASK, true>, kMt4TmaAdapt, FID, MASK);
 }
 
-int mt4_grid(const LocalArgs& a, bool tma, int fid, bool mask) {
+int mt4_grid(const LocalArgs& a, int kind, int fid, bool mask) {
   int dev = 0;
   cudaGetDevice(&dev);
   const int tiles = a.g.NR * a.g.NC;
-  int nc = mt4_clusters(dev, tma, fid, mask);
+  int nc = mt4_clusters(dev, kind, fid, mask);
   return (nc <= 0 || nc > tiles) ? tiles : nc;
 }
 
 template <int FID, bool MASK>
 cudaError_t launch_mt4_one(const LocalArgs& a, cudaStream_t st) {
   cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t cfg = mt4_config(mt4_grid(a, false, FID, MASK), false, attr);
+  cudaLaunchConfig_t cfg = mt4_config(mt4_grid(a, kMt4Cp, FID, MASK), false, attr);
   cfg.stream = st;
   return cudaLaunchKernelEx(&cfg, k_fused_mt4<FID, MASK>, a);
 }
 
-template <int FID, bool MASK>
+template <int FID, bool MASK, bool ADAPT>
 cudaError_t launch_mt4t_one(const LocalArgs& a, const Mt4Maps& maps, cudaStream_t st) {
   cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t cfg = mt4_config(mt4_grid(a, true, FID, MASK), true, attr);
+  cudaLaunchConfig_t cfg = mt4_config(mt4_grid(a, ADAPT ? kMt4TmaAdapt : kMt4Tma, FID, MASK), true, attr);
   cfg.stream = st;
-  return cudaLaunchKernelEx(&cfg, k_fused_mt4t<FID, MASK>, a, maps);
+  return cudaLaunchKernelEx(&cfg, k_fused_mt4t<FID, MASK, ADAPT>, a, maps);
+}
+
+template <bool ADAPT>
+cudaError_t launch_mt4t_fid(const LocalArgs& a, const Mt4Maps& maps, int fid, cudaStream_t st) {
+  const bool m = a.mask != nullptr;
+  switch (fid) {
+    case FID_L2:
+      return m ? launch_mt4t_one<FID_L2, true, ADAPT>(a, maps, st) : launch_mt4t_one<FID_L2, false, ADAPT>(a, maps, st);
+    case FID_L1:
+      return m ? launch_mt4t_one<FID_L1, true, ADAPT>(a, maps, st) : launch_mt4t_one<FID_L1, false, ADAPT>(a, maps, st);
+    default: return launch_mt4t_one<FID_SEG, false, ADAPT>(a, maps, st);
+  }
 }
 
 // cuTensorMapEncodeTiled from the driver (no link-time dependency on libcuda)
@@ -664,13 +801,11 @@ cudaError_t fused_mt4_prepare() {
 cudaError_t launch_fused_mt4(const LocalArgs& a, int fid, bool tma, cudaStream_t st) {
   const bool m = a.mask != nullptr;
   Mt4Maps maps;
-  if (tma && encode_maps(a, &maps)) {
-    switch (fid) {
-      case FID_L2: return m ? launch_mt4t_one<FID_L2, true>(a, maps, st) : launch_mt4t_one<FID_L2, false>(a, maps, st);
-      case FID_L1: return m ? launch_mt4t_one<FID_L1, true>(a, maps, st) : launch_mt4t_one<FID_L1, false>(a, maps, st);
-      default: return launch_mt4t_one<FID_SEG, false>(a, maps, st);
-    }
+  if (a.inner_tol2 > 0.0) {  // the adaptive stop exists in the tensor-copy kernel only
+    if (!encode_maps(a, &maps)) return cudaErrorNotSupported;
+    return launch_mt4t_fid<true>(a, maps, fid, st);
   }
+  if (tma && encode_maps(a, &maps)) return launch_mt4t_fid<false>(a, maps, fid, st);
   switch (fid) {
     case FID_L2: return m ? launch_mt4_one<FID_L2, true>(a, st) : launch_mt4_one<FID_L2, false>(a, st);
     case FID_L1: return m ? launch_mt4_one<FID_L1, true>(a, st) : launch_mt4_one<FID_L1, false>(a, st);

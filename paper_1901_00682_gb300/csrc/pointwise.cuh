@@ -61,11 +61,21 @@ __device__ __forceinline__ float p_target(float p, float du, float phat, const C
   return fmaf(c.pc, du, fmaf(c.pa, p, c.pb * phat));
 }
 
+// Projection onto [-lim, lim] (lim >= 0), the pointwise constraint set of the dual
+// field (|p| <= 1 on an edge, 0 on an edge of the image boundary): one min.xorsign.abs,
+// whose magnitude is min(|x|, lim) and whose sign is sign(x) xor sign(lim) = sign(x);
+// the value of fminf(fmaxf(x, -lim), lim) for every x that is not NaN.
+__device__ __forceinline__ float clamp_abs(float x, float lim) {
+  float r;
+  asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(x), "f"(lim));
+  return r;
+}
+
 // One dof of the p-step: q = p + tau_k Du, p_new = proj_[-1,1]((tau q + tau_k phat) /
 // (tau + tau_k)), pbar = p_new + theta_k (p_new - p).
 __device__ __forceinline__ void p_update(float& p, float& pbar, float du, float phat, const Coef& c) {
   const float t = p_target(p, du, phat, c);
-  const float pn = fminf(fmaxf(t, -1.0f), 1.0f);
+  const float pn = clamp_abs(t, 1.0f);
   pbar = fmaf(c.th, pn - p, pn);
   p = pn;
 }
