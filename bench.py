@@ -42,6 +42,7 @@ ENERGY_EVERY = 5
 METRIC = "Mpixel*iter/s at 4096^2 ROF"
 UNIT = "Mpixel*iter/s"
 ADAPT_CAP = 20  # inner iterations allowed per local solve under the adaptive stop
+ADAPT_TOL_F32 = 1e-4  # inner tolerance standing in for the paper's 1e-6 in float32
 WORKLOAD = "rof4096: ROF L2 denoising 4096x4096 fp32, alpha=8, 32x32 subdomains of 128x128, 10 inner/outer"
 SMEM_BYTES_PER_PX_ITER = 28  # minimum neighbour exchange per pixel per inner iteration
 JSTAR_FILE = os.path.join(ROOT, "tests", "golden", "jstar_rof4096_seed0.json")
@@ -641,10 +642,11 @@ def run_ours(args):
                                           "rel_err": (Jn - rec["J_star"]) / rec["J_star"],
                                           "reached": (Jn - rec["J_star"]) / rec["J_star"] <= 1e-4,
                                           "note": "m = infinity: energy evaluated once, after the timed run"}
-            # adaptive inner stopping (eq. stop_inner1): the paper's tolerance and a loose
-            # one, at most ADAPT_CAP inner iterations per local solve
+            # adaptive inner stopping (eq. stop_inner1), at most ADAPT_CAP inner iterations per
+            # local solve: the paper's tolerance (below what float32 iterates resolve: every
+            # solve runs to the cap), ADAPT_TOL_F32 (the float32 stand-in) and a loose one
             adaptive = {}
-            for itol in (1e-6, 1e-3):
+            for itol in (1e-6, ADAPT_TOL_F32, 1e-3):
                 key = f"inner_tol={itol:g}"
                 try:
                     pt = L.make_params(H, W, NR, NC, fidelity="l2", alpha=ALPHA, inner_iters=ADAPT_CAP,

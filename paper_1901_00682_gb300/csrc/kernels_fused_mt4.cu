@@ -67,9 +67,12 @@ struct Mt4Layout {
   static constexpr int UR = Q1 + (NW + 1) * BW;
   static constexpr int QL = UR + NW * SLOT;          // NW x 33 x 4: slot l = pbar2 of lane l's left edge
   static constexpr int F = QL + NW * SLOT;           // NW x 4 (column) x 32 (lane) x 4: f (or g), pair order
-  static constexpr int CO = F + NW * 4 * 32 * 4;     // kMaxSmemCoef x 8 coefficients
+  // kMaxSmemCoef x 16: the 8 coefficients of each inner iteration, each stored twice
+  // (sig sig ua ua ub ub s s pa pa pc pc pb pb th th) so that one 16-byte load gives two
+  // packed pairs
+  static constexpr int CO = F + NW * 4 * 32 * 4;
   static constexpr int kMaxSmemCoef = 64;
-  static constexpr int SU = CO + 8 * kMaxSmemCoef;   // staging of the next subdomain: u, f, p1 (BAND x 128 each)
+  static constexpr int SU = CO + 16 * kMaxSmemCoef;  // staging of the next subdomain: u, f, p1 (BAND x 128 each)
   static constexpr int SP2 = SU + 3 * BAND * BW;     // p2 window (BAND x P2S)
   static constexpr int XLT = SP2 + BAND * P2S;       // lamh above the tile (128)
   static constexpr int XPB = XLT + BW;               // p1 of the tile's bottom side (128)
@@ -196,7 +199,8 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int q = tid; q < 8 * K; q += NT) sCo[q] = reinterpret_cast<const float*>(A.coef)[q];  // K <= kMaxSmemCoef
+  for (int q = tid; q < 16 * K; q += NT)  // K <= kMaxSmemCoef
+    sCo[q] = reinterpret_cast<const float*>(A.coef)[(q >> 4) * 8 + ((q & 15) >> 1)];
   if (rank == 0 && w == 0) *reinterpret_cast<float4*>(sUB + j0) = make_float4(0.f, 0.f, 0.f, 0.f);  // u above the tile
   if (l < 4) smem[L::UR + w * L::SLOT + l] = 0.f;  // u left of the tile
   __syncthreads();
@@ -395,14 +399,12 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
     // the previous iteration held, instead of being moved back every iteration
 #pragma unroll 2
     for (int k = 0; k < K; ++k) {
-      Coef co;
-      {
-        const float4 ca = *reinterpret_cast<const float4*>(sCo + 8 * k);
-        const float4 cb = *reinterpret_cast<const float4*>(sCo + 8 * k + 4);
-        co = Coef{ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
-      }
-      const f32x2 SIG = pk2(co.sig, co.sig), UA = pk2(co.ua, co.ua), UB = pk2(co.ub, co.ub);
-      const f32x2 PA = pk2(co.pa, co.pa), PC = pk2(co.pc, co.pc), PB = pk2(co.pb, co.pb), TH = pk2(co.th, co.th);
+      const ulonglong2 cf0 = *reinterpret_cast<const ulonglong2*>(sCo + 16 * k);
+      const ulonglong2 cf1 = *reinterpret_cast<const ulonglong2*>(sCo + 16 * k + 4);
+      const ulonglong2 cf2 = *reinterpret_cast<const ulonglong2*>(sCo + 16 * k + 8);
+      const ulonglong2 cf3 = *reinterpret_cast<const ulonglong2*>(sCo + 16 * k + 12);
+      const f32x2 SIG = cf0.x, UA = cf0.y, UB = cf1.x, PA = cf2.x, PC = cf2.y, PB = cf3.x, TH = cf3.y;
+      const Coef co{lo2(SIG), lo2(UA), lo2(UB), lo2(cf1.y), lo2(PA), lo2(PC), lo2(PB), lo2(TH)};
       // adaptive stop: this thread's sums of (p^{k+1} - p^k)^2 and (p^{k+1})^2 over its dofs
       f32x2 AD = 0ull, AP = 0ull;
       auto res2 = [&](f32x2 pn, f32x2 po) {
