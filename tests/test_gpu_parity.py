@@ -1,6 +1,7 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same
 seeded inputs, at equal iteration counts.  Bar (stated per result):
   max |u_gpu - u_oracle| <= 5e-4 on [0, 1]-range images, relative energy error <= 1e-5,
+the dual field and the multipliers within their float32 error growth (p_tol, lam_tol),
 and bit-exact agreement between the fused and the plain GPU paths (they share the
 pointwise arithmetic).  Covers several tiles with ragged tails, every fidelity, the
 inpainting mask, the 1 x 1 grid, the full-dimension comparator, state export/import
@@ -18,6 +19,24 @@ pytestmark = pytest.mark.gpu
 
 U_TOL = 5e-4
 E_TOL = 1e-5
+U32 = 2.0 ** -24  # unit roundoff of float32
+
+
+def p_tol(n_steps):
+    """Tolerance of the dual field after n_steps inner iterations in all.  |p| <= 1, each
+    update of a dof rounds through at most 4 float32 operations, and the primal-dual
+    iteration carries earlier deviations forward without amplifying them, so the
+    distance to the float64 trajectory grows at most linearly: 4 u n_steps.  (Measured on
+    these cases: 0.1 u to 0.5 u per inner iteration.)"""
+    return 4.0 * U32 * n_steps
+
+
+def lam_tol(n_outer, inner, sigma, lam_max):
+    """Tolerance of the multipliers after n_outer outer iterations.  Each update adds
+    sigma times the jump of 2 p~^{n+1} - p~^n across an interface (three dual values on
+    each of two sides): the dual deviations contribute at most 6 sigma n_outer p_tol, and
+    the update's own rounding 4 u max(1, |lambda|) per outer iteration."""
+    return 6.0 * sigma * n_outer * p_tol(n_outer * inner) + 4.0 * U32 * n_outer * max(1.0, lam_max)
 
 
 def _gpu():
@@ -60,10 +79,17 @@ def _check(f, mask, n_outer, **kw):
     Jg = oracle.energy(pr, g["u"], f.astype(np.float64), mask)
     Jo = oracle.energy(pr, o.u, f.astype(np.float64), mask)
     assert abs(Jg - Jo) <= E_TOL * abs(Jo), (Jg, Jo)
-    # the dual field and the multipliers follow the same trajectory
-    assert np.abs(g["P1"] - o.P1).max() <= 1e-2 and np.abs(g["P2"] - o.P2).max() <= 1e-2
-    if o.lamh.size:
-        assert np.abs(g["lamh"] - o.lamh).max() <= 1e-2 * max(1.0, np.abs(o.lamh).max())
+    # the dual field and the multipliers follow the same trajectory, within the float32
+    # error growth of p_tol / lam_tol
+    K = kw.get("inner_iters", 10)
+    tau = kw.get("tau") or (1.0 if kw.get("fidelity") == "seg" else 50.0)
+    sigma = kw.get("sigma") or 0.5 / tau
+    tp = p_tol(n_outer * K)
+    assert np.abs(g["P1"] - o.P1).max() <= tp and np.abs(g["P2"] - o.P2).max() <= tp
+    for k in ("lamh", "lamv"):
+        ref = getattr(o, k)
+        if ref.size:
+            assert np.abs(g[k] - ref).max() <= lam_tol(n_outer, K, sigma, np.abs(ref).max()), k
     return s, g, o, du
 
 
@@ -140,7 +166,7 @@ def test_fulldim_parity():
     pr = oracle.Problem(64, 96, fidelity="l2", alpha=10.0)
     cp = oracle.cp_run(pr, f.astype(np.float64), 300)
     assert np.abs(g["u"] - cp.u).max() <= U_TOL
-    assert np.abs(g["P1"] - cp.p1).max() <= 1e-2
+    assert np.abs(g["P1"] - cp.p1).max() <= p_tol(300)
 
 
 def test_energy_and_gap_kernels():
@@ -237,7 +263,8 @@ def test_full_size_4096_sampled_parity():
     _, g, _, _ = _run_gpu(f, None, 2, **kw)
     _, o = _run_oracle(f, None, 2, **kw)
     assert np.abs(g["u"] - o.u).max() <= U_TOL
-    assert np.abs(g["lamh"] - o.lamh).max() <= 1e-3
+    assert np.abs(g["P1"] - o.P1).max() <= p_tol(20) and np.abs(g["P2"] - o.P2).max() <= p_tol(20)
+    assert np.abs(g["lamh"] - o.lamh).max() <= lam_tol(2, 10, 0.01, np.abs(o.lamh).max())
 
 
 @pytest.mark.slow
@@ -275,7 +302,7 @@ def test_maximum_size_sampled_subdomains(side):
         # the subdomain's p1 dofs: rows a*129 .. a*129 + 128 of the torn layout
         pg = st["P1"][a * 129:(a + 1) * 129, b * 128:(b + 1) * 128].cpu().numpy().astype(np.float64)
         po = o.P1[(a - r0) * 129:(a - r0 + 1) * 129, (b - c0) * 128:(b - c0 + 1) * 128]
-        assert np.abs(pg - po).max() <= 1e-2, (a, b)
+        assert np.abs(pg - po).max() <= p_tol(n_outer * 10), (a, b)
     del st, fd
     torch.cuda.empty_cache()
 
