@@ -35,13 +35,13 @@ __device__ __forceinline__ f32x2 pk2(float lo, float hi) {
   return r;
 }
 __device__ __forceinline__ float lo2(f32x2 v) {
-  float a, b;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+  float a;
+  asm("mov.b64 {%0, _}, %1;" : "=f"(a) : "l"(v));
   return a;
 }
 __device__ __forceinline__ float hi2(f32x2 v) {
-  float a, b;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+  float b;
+  asm("mov.b64 {_, %0}, %1;" : "=f"(b) : "l"(v));
   return b;
 }
 __device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {

@@ -181,3 +181,22 @@ def test_adaptive_micro_tile_matches_fixed_count_when_tol_is_tiny(cuda_lib):
         s.iterate(5)
         u_f = s.get_u(torch.empty_like(fd)).cpu().numpy().astype(np.float64)
     assert np.array_equal(u_a, u_f)
+
+
+@pytest.mark.parametrize("K", [1, 2, 3])
+def test_adaptive_micro_tile_small_caps(cuda_lib, K):
+    """Caps of 1 to 3 inner iterations in the micro-tile kernel: with K = 1 no decision is
+    taken (every count is 1); with K = 2, 3 the decision on iteration k is taken in
+    iteration k + 1 and the counts stay in [1, K]; the iterates match the oracle run at
+    the same counts."""
+    H, W, N, tol = 512, 512, 6, 2e-2
+    f, _ = synth.rof_image(H, W, 12, 0.05, 41)
+    u, counts, J = _run_gpu(f, 4, 4, N, tol, K, alpha=8.0)
+    assert counts.min() >= 1 and counts.max() <= K
+    if K == 1:
+        assert np.all(counts == 1)
+    pr = oracle.Problem(H, W, 4, 4, fidelity="l2", alpha=8.0, inner=K)
+    st = oracle.dd_run(pr, f, N, counts=counts)
+    assert np.abs(u - st.u).max() <= 5e-4
+    Jo = oracle.energy(pr, st.u, f)
+    assert abs(J - Jo) <= 1e-5 * abs(Jo)
