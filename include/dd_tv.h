@@ -321,13 +321,14 @@ typedef struct {
 } dd_tv_batch_image;
 
 typedef struct {
-  int tile;               /* subdomain side: 128 (persistent clusters of 2 x 4 pixel
-                             micro-tiles over the work list) or 64 (one CTA per
-                             subdomain); other sides return DD_TV_EUNSUPPORTED          */
+  int tile;               /* subdomain side: 128 (persistent clusters over the work
+                             list, see variant) or 64 (one CTA per subdomain); other
+                             sides return DD_TV_EUNSUPPORTED                            */
   int inner_iters;        /* 1..DD_TV_MAX_INNER                                        */
   double tau0, sigma0;    /* initial inner steps (Section 5: 10 and 1/80)               */
-  int variant;            /* must be 0: persistent clusters over the batch's work list,
-                             2 x 4 pixel micro-tiles per thread                       */
+  int variant;            /* 0: 4 x 4 pixel micro-tiles per thread (2 x 4 when
+                             inner_iters > 64); 2 (tile 128 only): 2 x 4 micro-tiles.
+                             Both give the same bits; anything else: DD_TV_EINVAL      */
 } dd_tv_batch_params;
 
 /* Validates and allocates the batch (images[n], n >= 1); *out = NULL on error. */

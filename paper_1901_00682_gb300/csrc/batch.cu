@@ -108,7 +108,7 @@ cudaError_t outer_once(dd_tv_batch* b, int par) {
   ba.tile_img = b->d_tile_img;
   ba.tile_base = b->d_tile_base;
   ba.write_set = 1 - par;
-  return launch_fused_batch(ba, b->total_tiles, b->p.tile, b->stream);
+  return launch_fused_batch(ba, b->total_tiles, b->p.tile, b->p.variant, b->p.inner_iters, b->stream);
 }
 
 void drop_batch_graphs(dd_tv_batch* b) {
@@ -172,7 +172,8 @@ int dd_tv_batch_create(dd_tv_batch** out, const dd_tv_batch_image* images, int n
   if (p->inner_iters < 1 || p->inner_iters > DD_TV_MAX_INNER) return bfail(nullptr, DD_TV_EINVAL, "bad inner_iters");
   if (!(p->tau0 > 0) || !(p->sigma0 > 0) || p->tau0 * p->sigma0 > 0.125 * (1 + 1e-12))
     return bfail(nullptr, DD_TV_EINVAL, "tau0, sigma0 must be > 0 with tau0 sigma0 <= 1/8");
-  if (p->variant != 0) return bfail(nullptr, DD_TV_EINVAL, "batch variant must be 0");
+  if (p->variant != 0 && !(p->variant == 2 && p->tile == 128))
+    return bfail(nullptr, DD_TV_EINVAL, "batch variant must be 0 (or 2 with 128 x 128 subdomains)");
   for (int i = 0; i < n; ++i) {
     const dd_tv_batch_image& m = images[i];
     if (m.height < T || m.width < T || m.height % T || m.width % T)

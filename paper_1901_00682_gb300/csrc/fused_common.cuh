@@ -202,6 +202,7 @@ struct FidC {
 struct BatchTiles {
   const BatchArgs& B;
   int total;
+  static constexpr bool kBatch = true;
   __device__ int count() const { return total; }
   __device__ int inner() const { return B.args[0].K; }
   __device__ int image(int t) const { return B.tile_img[t]; }

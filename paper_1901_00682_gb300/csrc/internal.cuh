@@ -105,9 +105,10 @@ cudaError_t launch_interface_batch(const BatchIfaceArgs& a, int total4, cudaStre
 
 // ---- kernels_fused.cu
 // All tiles of all images of a batch, one launch (BatchArgs.write_set selects the strips);
-// tile: the subdomain side, 128 (persistent 2 x 4 micro-tile kernel) or 64 (one CTA per
-// subdomain).
-cudaError_t launch_fused_batch(const BatchArgs& B, int total_tiles, int tile, cudaStream_t st);
+// tile: the subdomain side, 128 (persistent micro-tile kernels: variant 0 the 4 x 4 one
+// when K <= fused_mt4_max_inner(), else and for variant 2 the 2 x 4 one) or 64 (one CTA
+// per subdomain).
+cudaError_t launch_fused_batch(const BatchArgs& B, int total_tiles, int tile, int variant, int K, cudaStream_t st);
 // One outer iteration's local solves, all tiles, fused (returns cudaErrorInvalidValue
 // if no fused configuration fits the tile shape).
 cudaError_t launch_fused_local(const LocalArgs& a, int fidelity, int variant, cudaStream_t st);
@@ -141,6 +142,10 @@ bool fused_mt4_supported(const LocalArgs& a);
 // cannot be encoded.
 cudaError_t launch_fused_mt4(const LocalArgs& a, int fidelity, bool tma, cudaStream_t st);
 cudaError_t fused_mt4_prepare();
+// The same kernel (cp.async copies) over the work list of a batch: every image's arrays
+// 16-byte aligned, inner count <= fused_mt4_max_inner().
+cudaError_t launch_fused_mt4_batch(const BatchArgs& B, int total_tiles, cudaStream_t st);
+int fused_mt4_max_inner();
 
 // ---- kernels_plain.cu
 // phat = p~ -+ tau lambda on the interface sides, pbar = p~; full arrays.

@@ -469,8 +469,10 @@ cudaError_t fused_prepare() {
   return fused_mt4_prepare();
 }
 
-cudaError_t launch_fused_batch(const BatchArgs& B, int total_tiles, int tile, cudaStream_t st) {
-  if (tile == 128) return launch_fused_mt_batch(B, total_tiles, st);
+cudaError_t launch_fused_batch(const BatchArgs& B, int total_tiles, int tile, int variant, int K, cudaStream_t st) {
+  if (tile == 128)  // variant 0: 4 x 4 micro-tiles (K within its shared coefficient table); 2: 2 x 4
+    return variant == 0 && K <= fused_mt4_max_inner() ? launch_fused_mt4_batch(B, total_tiles, st)
+                                                       : launch_fused_mt_batch(B, total_tiles, st);
   if (tile != 64) return cudaErrorInvalidValue;
   // 64 x 64 subdomains: one CTA of 64 x 8 threads per subdomain
   k_fused_tile_batch<64, 8, 8, 1><<<dim3(1, total_tiles, 1), dim3(64, 8, 1), SmemLayout<64, 8, 8>::BYTES, st>>>(B);

@@ -142,9 +142,34 @@ __device__ __forceinline__ void tma_fence_smem() { asm volatile("fence.proxy.asy
 
 __device__ __forceinline__ float lane4(f32x2 v, int h) { return h ? hi2(v) : lo2(v); }
 
-template <int FID, bool MASK, bool TMA, bool ADAPT>
-__device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps* M, const int first,
-                                               const int stride) {
+// The subdomains of one image (tile t = a N_c + b), its fidelity fixed at compile time.
+// The batch kernel runs the same body over BatchTiles (fused_common.cuh): every
+// subdomain with its image's geometry, parameters, strips and fidelity.
+template <int FID>
+struct Mt4One {
+  const LocalArgs& A;
+  static constexpr bool kBatch = false;
+  __device__ int count() const { return A.g.NR * A.g.NC; }
+  __device__ int inner() const { return A.K; }
+  __device__ int image(int) const { return 0; }
+  __device__ const LocalArgs& args(int) const { return A; }
+  __device__ int local(int t) const { return t; }
+  __device__ Strips out(int) const { return A.out; }
+  __device__ int* err() const { return A.err; }
+  template <class Body>
+  __device__ void dispatch(int, Body&& body) const {
+    body(FidC<FID>{});
+  }
+};
+
+// the coefficient sets of an image into shared memory, each coefficient twice
+__device__ __forceinline__ void load_coef_dup(float* sCo, const Coef* coef, int K, int tid, int nt) {
+  for (int q = tid; q < 16 * K; q += nt)  // K <= kMaxSmemCoef
+    sCo[q] = reinterpret_cast<const float*>(coef)[(q >> 4) * 8 + ((q & 15) >> 1)];
+}
+
+template <bool MASK, bool TMA, bool ADAPT, class Src>
+__device__ __forceinline__ void fused_mt4_body(const Src& S, const Mt4Maps* M, const int first, const int stride) {
   using L = Mt4Layout;
   constexpr int NW = L::NW, CL = L::CL, BAND = L::BAND, NT = L::NT, BW = L::BW;
   extern __shared__ __align__(128) float smem[];
@@ -156,17 +181,15 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
   const uint32_t mbL = mbU + 16;  // tensor loads of the staged subdomain (TMA)
   const uint32_t mbR = mbU + 24;  // reduction phases of the adaptive stop, two mbarriers (parity)
   static_assert(!ADAPT || TMA, "the adaptive stop keeps the rolled-back u in the tensor-copy out-buffer");
+  static_assert(!(Src::kBatch && (TMA || ADAPT || MASK)), "the batch runs the cp.async kernel, fixed counts, no mask");
 
-  const Grid g = A.g;
-  const int T = g.NR * g.NC;
+  const int T = S.count();
   const int rank = (int)blockIdx.x;
   const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
   const int j0 = 4 * l;              // the lane's first column in the tile
   const int lr0 = 4 * w;             // the warp's first row in the band
   const int i0 = rank * BAND + lr0;  // ... in the tile
-  const int W2 = g.W + g.NC;
-  const float tau = A.tau;
-  const int K = A.K;
+  const int K = S.inner();
   const bool last_row_here = rank == CL - 1 && w == NW - 1;
   // the tile's bottom side is updated by warp 2 of the last CTA (the last warp, which
   // holds the last row, already waits for halos and pushes rows); warp 1 updates the
@@ -199,8 +222,8 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int q = tid; q < 16 * K; q += NT)  // K <= kMaxSmemCoef
-    sCo[q] = reinterpret_cast<const float*>(A.coef)[(q >> 4) * 8 + ((q & 15) >> 1)];
+  if (!Src::kBatch) load_coef_dup(sCo, S.args(0).coef, K, tid, NT);
+  int cur_img = Src::kBatch ? -1 : 0;  // image whose coefficients are in sCo
   if (rank == 0 && w == 0) *reinterpret_cast<float4*>(sUB + j0) = make_float4(0.f, 0.f, 0.f, 0.f);  // u above the tile
   if (l < 4) smem[L::UR + w * L::SLOT + l] = 0.f;  // u left of the tile
   __syncthreads();
@@ -214,7 +237,11 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
   cluster_wait();
 
   auto prefetch = [&](int t) {
-    const int a = t / g.NC, b = t - a * g.NC;
+    const LocalArgs& A = S.args(t);
+    const Grid g = A.g;
+    const int W2 = g.W + g.NC;
+    const int lt = S.local(t);
+    const int a = lt / g.NC, b = lt - a * g.NC;
     const int c0 = b * 128;
     const int gb = a * 128 + rank * BAND;  // image row of the band's first row
     if (TMA) {
@@ -235,13 +262,22 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
         const int grow = gb + row + (fld == 2 ? a : 0);
         cp_async16(smem + L::SU + fld * BAND * BW + row * BW + 4 * ch, base + (size_t)grow * g.W + c0 + 4 * ch);
       }
+      if (!Src::kBatch || (W2 & 3) == 0) {
 #pragma unroll
-      for (int m = 0; m < 5; ++m) {  // p2 window: BAND rows x 33 chunks
-        const int q = tid + NT * m;
-        if (q < BAND * 33) {
-          const int row = q / 33, ch = q - row * 33;
-          cp_async16(smem + L::SP2 + row * L::P2S + 4 * ch,
-                     A.P2 + (size_t)(gb + row) * W2 + c0 + b - (b & 3) + 4 * ch);
+        for (int m = 0; m < 5; ++m) {  // p2 window: BAND rows x 33 chunks
+          const int q = tid + NT * m;
+          if (q < BAND * 33) {
+            const int row = q / 33, ch = q - row * 33;
+            cp_async16(smem + L::SP2 + row * L::P2S + 4 * ch,
+                       A.P2 + (size_t)(gb + row) * W2 + c0 + b - (b & 3) + 4 * ch);
+          }
+        }
+      } else {  // rows not 16-byte aligned (a batch image with W + N_c not a multiple of 4):
+                // the tile's 129 p2 columns one by one, at the same place in the window
+        const int o = b & 3;
+        for (int q = tid; q < BAND * 129; q += NT) {
+          const int row = q / 129, col = q - row * 129;
+          cp_async4(smem + L::SP2 + row * L::P2S + o + col, A.P2 + (size_t)(gb + row) * W2 + c0 + b + col);
         }
       }
     }
@@ -282,7 +318,13 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
   uint32_t gred = 0;              // adaptive stop: reduction phases sent (and consumed) so far
 
   for (int t = first; t < T; t += stride, ++nsub) {
-    const int a = t / g.NC, b = t - a * g.NC;
+    const LocalArgs& A = S.args(t);
+    const Grid g = A.g;
+    const int W2 = g.W + g.NC;
+    const float tau = A.tau;
+    const Strips out = S.out(t);
+    const int lt = S.local(t);
+    const int a = lt / g.NC, b = lt - a * g.NC;
     const int c0 = b * 128;
     const int gb = a * 128 + rank * BAND;
     const int o = b & 3;
@@ -297,6 +339,8 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
     const bool right_rows = s_rgt && w == 1 && l < BAND;
     const int r_slot = (l >> 2) * L::SLOT + 4 * 32 + 2 * (l & 1) + ((l >> 1) & 1);
     float pr_s = 0.f, hr_s = 0.f;
+    S.dispatch(t, [&](auto fidc) {
+    constexpr int FID = decltype(fidc)::value;
     // pairs [column c][e]: rows (e, e + 2) of column j0 + c
     f32x2 U[4][2], P1[4][2], P2[4][2], H1[4][2], H2[4][2], Q1[4][2], Q2[4][2];
     uint32_t in_d = 0;  // bit 4c + r: pixel (row r, column j0 + c) lies in the inpainting domain
@@ -305,6 +349,10 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
     cp_async_wait_all();
     if (TMA && !mbar_wait(mbL, nsub & 1)) timed_out = true;
     __syncthreads();  // staging landed; the previous subdomain's shared arrays are free
+    if (Src::kBatch && S.image(t) != cur_img) {  // visible after the barrier that follows the unpack
+      load_coef_dup(sCo, A.coef, K, tid, NT);
+      cur_img = S.image(t);
+    }
     if (TMA && tid == 0 && pa >= 0) {  // the previous subdomain's u and p1 bands
       tma_store_2d(&M->u, smem + L::OU, pc0, pgb);
       tma_store_2d(&M->p1, smem + L::OP1, pc0, pgb + pa);
@@ -607,20 +655,20 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
       float* p2row = A.P2 + (size_t)gi * W2 + c0 + b + j0;
 #pragma unroll
       for (int c = 0; c < 4; ++c) p2row[c] = lane4(P2[c][e], h);
-      if (l == 0 && s_lft) A.out.SL[(size_t)(b - 1) * g.H + gi] = lane4(P2[0][e], h);
+      if (l == 0 && s_lft) out.SL[(size_t)(b - 1) * g.H + gi] = lane4(P2[0][e], h);
     }
     if (right_rows) {
       const int gi = gb + l;
       A.P2[(size_t)gi * W2 + c0 + 128 + b] = pr_s;
-      A.out.SR[(size_t)b * g.H + gi] = pr_s;
+      out.SR[(size_t)b * g.H + gi] = pr_s;
     }
     if (i0 == 0 && s_top)
-      *reinterpret_cast<float4*>(A.out.ST + (ptrdiff_t)(a - 1) * g.W + c0 + j0) =
+      *reinterpret_cast<float4*>(out.ST + (ptrdiff_t)(a - 1) * g.W + c0 + j0) =
           make_float4(lo2(P1[0][0]), lo2(P1[1][0]), lo2(P1[2][0]), lo2(P1[3][0]));
     if (last_row_here && s_bot) {
       const float4 v = *reinterpret_cast<const float4*>(smem + L::PBS + j0);
       *reinterpret_cast<float4*>(A.P1 + (size_t)(a * 128 + 128 + a) * g.W + c0 + j0) = v;
-      *reinterpret_cast<float4*>(A.out.SB + (size_t)a * g.W + c0 + j0) = v;
+      *reinterpret_cast<float4*>(out.SB + (size_t)a * g.W + c0 + j0) = v;
     }
     if (TMA) {
       tma_fence_smem();  // the out-buffer writes become visible to the tensor stores
@@ -628,6 +676,7 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
       pc0 = c0;
       pgb = gb;
     }
+    });  // dispatch
   }
   if (TMA && pa >= 0) {  // the last subdomain's bands
     __syncthreads();
@@ -641,17 +690,22 @@ __device__ __forceinline__ void fused_mt4_body(const LocalArgs& A, const Mt4Maps
   cp_async_wait_all();
   cluster_arrive<true>();  // no CTA leaves while a neighbour may still write into it
   cluster_wait();
-  if (timed_out) atomicOr(A.err, 1);
+  if (timed_out) atomicOr(S.err(), 1);
 }
 
 template <int FID, bool MASK>
 __global__ void __launch_bounds__(Mt4Layout::NT, 3) k_fused_mt4(const LocalArgs A) {
-  fused_mt4_body<FID, MASK, false, false>(A, nullptr, blockIdx.y, gridDim.y);
+  fused_mt4_body<MASK, false, false>(Mt4One<FID>{A}, nullptr, blockIdx.y, gridDim.y);
 }
 
 template <int FID, bool MASK, bool ADAPT>
 __global__ void __launch_bounds__(Mt4Layout::NT, 3) k_fused_mt4t(const LocalArgs A, const __grid_constant__ Mt4Maps M) {
-  fused_mt4_body<FID, MASK, true, ADAPT>(A, &M, blockIdx.y, gridDim.y);
+  fused_mt4_body<MASK, true, ADAPT>(Mt4One<FID>{A}, &M, blockIdx.y, gridDim.y);
+}
+
+// the batch's work list: every subdomain with its image's descriptor and fidelity
+__global__ void __launch_bounds__(Mt4Layout::NT, 3) k_fused_mt4_batch(const BatchArgs B, int total) {
+  fused_mt4_body<false, false, false>(BatchTiles{B, total}, nullptr, blockIdx.y, gridDim.y);
 }
 
 // kernel kinds: cp.async copies, tensor copies, tensor copies with the adaptive stop
@@ -693,6 +747,29 @@ cudaError_t prepare_kernel(Kern kern, int kind, int fid, bool mask) {
   int dev = 0;
   cudaGetDevice(&dev);
   mt4_clusters(dev, kind, fid, mask) = n;
+  return cudaSuccess;
+}
+
+// clusters of the batch kernel resident at once, per device
+int& mt4_batch_clusters(int dev) {
+  static int n[64] = {};
+  return n[dev & 63];
+}
+
+cudaError_t prepare_mt4_batch() {
+  cudaError_t e = cudaFuncSetAttribute(k_fused_mt4_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Mt4Layout::BYTES);
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = mt4_config(1024, false, attr);
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_fused_mt4_batch, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  mt4_batch_clusters(dev) = n;
   return cudaSuccess;
 }
 
@@ -791,8 +868,21 @@ bool fused_mt4_supported(const LocalArgs& a) {
          al16(a.P1) && al16(a.P2) && al16(a.lamh) && al16(a.lamv) && al16(a.out.ST) && al16(a.out.SB);
 }
 
+int fused_mt4_max_inner() { return Mt4Layout::kMaxSmemCoef; }
+
+cudaError_t launch_fused_mt4_batch(const BatchArgs& B, int total_tiles, cudaStream_t st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int nc = mt4_batch_clusters(dev);
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = mt4_config((nc <= 0 || nc > total_tiles) ? total_tiles : nc, false, attr);
+  cfg.stream = st;
+  return cudaLaunchKernelEx(&cfg, k_fused_mt4_batch, B, total_tiles);
+}
+
 cudaError_t fused_mt4_prepare() {
   cudaError_t e;
+  if ((e = prepare_mt4_batch()) != cudaSuccess) return e;
   if ((e = prepare_mt4_one<FID_L2, false>()) != cudaSuccess) return e;
   if ((e = prepare_mt4_one<FID_L2, true>()) != cudaSuccess) return e;
   if ((e = prepare_mt4_one<FID_L1, false>()) != cudaSuccess) return e;

@@ -155,8 +155,9 @@ class Workload:
 
 
 def batch_workload(n_images: int = 64, seed: int = 0):
-    """The mixed batch: image i has side s in {256, 512, 1024, 2048} and aspect in
-    {1:1, 2:1 landscape, 1:2 portrait} (both drawn uniformly); even i is ROF denoising
+    """The mixed batch: image i has short side s in {256, 512, 1024, 2048} and aspect in
+    {1:1 (s x s), 2:1 landscape (s x 2s), 1:2 portrait (2s x s)} (both drawn uniformly;
+    mean area 2.32 Mpixel); even i is ROF denoising
     (sigma 0.05, alpha 10), odd i two-phase segmentation of a noisy piecewise-constant
     image (sigma 0.05, c1 0.2, c2 0.8, alpha 20).  Returns a list of dicts with the
     image (float32), its shape, fidelity and parameters; image i uses seed 1000*seed+i."""
@@ -165,7 +166,7 @@ def batch_workload(n_images: int = 64, seed: int = 0):
     for i in range(n_images):
         side = int(rng.choice([256, 512, 1024, 2048]))
         aspect = int(rng.integers(0, 3))
-        h, w = (side, side) if aspect == 0 else ((side // 2, side) if aspect == 1 else (side, side // 2))
+        h, w = (side, side) if aspect == 0 else ((side, 2 * side) if aspect == 1 else (2 * side, side))
         shapes = max(4, (h * w) // (4096 * 4096 // 400))
         f, clean = rof_image(h, w, shapes, 0.05, 1000 * seed + i)
         if i % 2 == 0:

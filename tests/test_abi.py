@@ -137,6 +137,14 @@ def test_batch_create_rejects_invalid(lib, field, value, code, needle):
     assert needle in lib.dd_tv_batch_last_error(None).decode()
 
 
+def test_batch_variant_2_needs_tile_128(lib):
+    from paper_1901_00682_gb300 import _lib
+    arr, bp = _batch_args(tile=64, height=128, variant=2)
+    h = ctypes.c_void_p()
+    assert lib.dd_tv_batch_create(ctypes.byref(h), arr, 2, ctypes.byref(bp)) == _lib.EINVAL and not h.value
+    assert "variant" in lib.dd_tv_batch_last_error(None).decode()
+
+
 def test_batch_create_rejects_empty_batch(lib):
     from paper_1901_00682_gb300 import _lib
     arr, bp = _batch_args()

@@ -29,13 +29,16 @@ def _images():
     return out
 
 
-@pytest.mark.parametrize("tile", [128, 64])
-def test_batch_equals_single_image_solves_bitwise(tile):
-    """The batch kernels (128: persistent clusters over the work list; 64: one CTA per
-    subdomain) give each image the bits of its own solve."""
+@pytest.mark.parametrize("tile,variant", [(128, 0), (128, 2), (64, 0)])
+def test_batch_equals_single_image_solves_bitwise(tile, variant):
+    """The batch kernels (128: persistent clusters over the work list, 4 x 4 micro-tiles
+    (variant 0) or 2 x 4 (variant 2); 64: one CTA per subdomain) give each image the
+    bits of its own solve.  Every image here has W + N_c not a multiple of 4, so the
+    4 x 4 kernel copies their p2 rows 4 bytes at a time (the full-workload test below
+    covers the 16-byte copies)."""
     L = _lib()
     ims = _images()
-    b = L.Batch(ims, inner_iters=10, tile=tile)
+    b = L.Batch(ims, inner_iters=10, tile=tile, variant=variant)
     fs = [torch.from_numpy(m["f"]).cuda() for m in ims]
     b.load(fs)
     b.iterate(13)
@@ -70,6 +73,48 @@ def test_batch_matches_oracle():
         assert np.abs(u - st.u).max() <= 5e-4
         Jo = oracle.energy(pr, st.u, m["f"].astype(np.float64))
         assert abs(b.energy(k) - Jo) <= 1e-5 * abs(Jo)
+
+
+def test_batch_variants_bitwise_on_the_full_workload():
+    """The 4 x 4 and 2 x 4 batch kernels give the same bits on the benchmark's batch."""
+    L = _lib()
+    ims = synth.batch_workload(64, 0)
+    fs = [torch.from_numpy(m["f"]).cuda() for m in ims]
+    us = []
+    for variant in (0, 2):
+        b = L.Batch(ims, inner_iters=10, variant=variant)
+        b.load(fs)
+        b.iterate(3)
+        us.append([b.get_u(k, torch.empty_like(fs[k])) for k in range(len(ims))])
+        b.close()
+    torch.cuda.synchronize()
+    for k in range(len(ims)):
+        assert torch.equal(us[0][k], us[1][k]), k
+
+
+def test_full_batch_workload_parity():
+    """The benchmark's 64-image batch (synth.batch_workload(64, 0): 168 Mpixel, short
+    sides 256 to 2048, aspects 1:1, 2:1, 1:2, ROF and segmentation) in the benchmark's
+    launch configuration (128 x 128 subdomains, K = 10, one graph): after 2 outer
+    iterations every image matches the FP64 oracle (5e-4 in u, 1e-5 in J)."""
+    L = _lib()
+    ims = synth.batch_workload(64, 0)
+    b = L.Batch(ims, inner_iters=10)
+    fs = [torch.from_numpy(m["f"]).cuda() for m in ims]
+    b.load(fs)
+    b.iterate(2)
+    torch.cuda.synchronize()
+    for k, m in enumerate(ims):
+        u = b.get_u(k, torch.empty_like(fs[k])).cpu().numpy().astype(np.float64)
+        tau = 1.0 if m["fidelity"] == "seg" else 50.0
+        pr = oracle.Problem(m["height"], m["width"], m["height"] // 128, m["width"] // 128, fidelity=m["fidelity"],
+                            alpha=m["alpha"], c1=m["c1"], c2=m["c2"], tau=tau, inner=10)
+        f64 = m["f"].astype(np.float64)
+        st = oracle.dd_run(pr, f64, 2)
+        assert np.abs(u - st.u).max() <= 5e-4, k
+        Jo = oracle.energy(pr, st.u, f64)
+        assert abs(b.energy(k) - Jo) <= 1e-5 * abs(Jo), k
+    b.close()
 
 
 def test_batch_rejects_bad_shapes():
