@@ -162,6 +162,35 @@ struct Mt4One {
   }
 };
 
+// A batch image's descriptor as the batch kernel keeps it in shared memory: its
+// LocalArgs, the strips it writes this launch, its first tile in the work list, its
+// fidelity and its index.
+struct Mt4BatchDesc {
+  LocalArgs A;
+  Strips out;
+  int base, fid, img, pad;
+};
+static_assert(sizeof(LocalArgs) % 4 == 0 && sizeof(Strips) % 4 == 0 && sizeof(Mt4BatchDesc) % 16 == 0,
+              "descriptors copied word by word");
+
+// every thread of the CTA copies words of image img's descriptor into d (a barrier must
+// follow before d is read)
+__device__ __forceinline__ void load_batch_desc(Mt4BatchDesc* d, const BatchArgs& B, int img, int tid, int nt) {
+  constexpr int kA = sizeof(LocalArgs) / 4, kS = sizeof(Strips) / 4, kN = sizeof(Mt4BatchDesc) / 4;
+  const uint32_t* a = reinterpret_cast<const uint32_t*>(B.args + img);
+  const uint32_t* st = reinterpret_cast<const uint32_t*>(B.strips + 2 * img + B.write_set);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(d);
+  for (int q = tid; q < kN; q += nt) {
+    uint32_t v = 0;
+    if (q < kA) v = a[q];
+    else if (q < kA + kS) v = st[q - kA];
+    else if (q == kA + kS) v = (uint32_t)B.tile_base[img];
+    else if (q == kA + kS + 1) v = (uint32_t)B.fid[img];
+    else if (q == kA + kS + 2) v = (uint32_t)img;
+    dst[q] = v;
+  }
+}
+
 // the coefficient sets of an image into shared memory, each coefficient twice
 __device__ __forceinline__ void load_coef_dup(float* sCo, const Coef* coef, int K, int tid, int nt) {
   for (int q = tid; q < 16 * K; q += nt)  // K <= kMaxSmemCoef
@@ -224,6 +253,15 @@ __device__ __forceinline__ void fused_mt4_body(const Src& S, const Mt4Maps* M, c
   }
   if (!Src::kBatch) load_coef_dup(sCo, S.args(0).coef, K, tid, NT);
   int cur_img = Src::kBatch ? -1 : 0;  // image whose coefficients are in sCo
+  // batch: the descriptors of the current and of the next subdomain's image, in the P1
+  // out-buffer region (unused by the cp.async kernel); a subdomain of the image already
+  // held reuses its slot, so the work list is read from global memory once per subdomain
+  // (its image index, loaded a subdomain ahead) and a descriptor once per image change
+  Mt4BatchDesc* const dsc = reinterpret_cast<Mt4BatchDesc*>(smem + L::OP1);
+  int cur = 0;  // slot of the current subdomain's descriptor
+  if constexpr (Src::kBatch) {
+    if (first < T) load_batch_desc(&dsc[0], S.B, S.B.tile_img[first], tid, NT);
+  }
   if (rank == 0 && w == 0) *reinterpret_cast<float4*>(sUB + j0) = make_float4(0.f, 0.f, 0.f, 0.f);  // u above the tile
   if (l < 4) smem[L::UR + w * L::SLOT + l] = 0.f;  // u left of the tile
   __syncthreads();
@@ -236,11 +274,9 @@ __device__ __forceinline__ void fused_mt4_body(const Src& S, const Mt4Maps* M, c
   cluster_arrive<true>();  // barriers initialised and armed everywhere before any halo is sent
   cluster_wait();
 
-  auto prefetch = [&](int t) {
-    const LocalArgs& A = S.args(t);
+  auto prefetch = [&](int t, const LocalArgs& A, const int lt) {
     const Grid g = A.g;
     const int W2 = g.W + g.NC;
-    const int lt = S.local(t);
     const int a = lt / g.NC, b = lt - a * g.NC;
     const int c0 = b * 128;
     const int gb = a * 128 + rank * BAND;  // image row of the band's first row
@@ -312,18 +348,25 @@ __device__ __forceinline__ void fused_mt4_body(const Src& S, const Mt4Maps* M, c
     if (l == 0) mbar_arrive_expect_tx(mbQ, kHaloBytes);
   };
 
-  if (first < T) prefetch(first);
+  if (first < T) {
+    if constexpr (Src::kBatch)
+      prefetch(first, dsc[0].A, first - dsc[0].base);
+    else
+      prefetch(first, S.args(first), S.local(first));
+  }
   uint32_t nsub = 0;             // subdomains started (phase of mbL)
   int pa = -1, pc0 = 0, pgb = 0;  // previous subdomain, whose u and p1 wait in the out-buffer (TMA)
   uint32_t gred = 0;              // adaptive stop: reduction phases sent (and consumed) so far
 
   for (int t = first; t < T; t += stride, ++nsub) {
-    const LocalArgs& A = S.args(t);
+    const LocalArgs& A = Src::kBatch ? dsc[cur].A : S.args(t);
     const Grid g = A.g;
     const int W2 = g.W + g.NC;
     const float tau = A.tau;
-    const Strips out = S.out(t);
-    const int lt = S.local(t);
+    const Strips out = Src::kBatch ? dsc[cur].out : S.out(t);
+    const int lt = Src::kBatch ? t - dsc[cur].base : S.local(t);
+    // batch: the next subdomain's image, loaded while this one's staging lands
+    const int img_next = (Src::kBatch && t + stride < T) ? S.image(t + stride) : 0;
     const int a = lt / g.NC, b = lt - a * g.NC;
     const int c0 = b * 128;
     const int gb = a * 128 + rank * BAND;
@@ -339,7 +382,7 @@ __device__ __forceinline__ void fused_mt4_body(const Src& S, const Mt4Maps* M, c
     const bool right_rows = s_rgt && w == 1 && l < BAND;
     const int r_slot = (l >> 2) * L::SLOT + 4 * 32 + 2 * (l & 1) + ((l >> 1) & 1);
     float pr_s = 0.f, hr_s = 0.f;
-    S.dispatch(t, [&](auto fidc) {
+    auto body = [&](auto fidc) {
     constexpr int FID = decltype(fidc)::value;
     // pairs [column c][e]: rows (e, e + 2) of column j0 + c
     f32x2 U[4][2], P1[4][2], P2[4][2], H1[4][2], H2[4][2], Q1[4][2], Q2[4][2];
@@ -349,9 +392,9 @@ __device__ __forceinline__ void fused_mt4_body(const Src& S, const Mt4Maps* M, c
     cp_async_wait_all();
     if (TMA && !mbar_wait(mbL, nsub & 1)) timed_out = true;
     __syncthreads();  // staging landed; the previous subdomain's shared arrays are free
-    if (Src::kBatch && S.image(t) != cur_img) {  // visible after the barrier that follows the unpack
+    if (Src::kBatch && dsc[cur].img != cur_img) {  // visible after the barrier that follows the unpack
       load_coef_dup(sCo, A.coef, K, tid, NT);
-      cur_img = S.image(t);
+      cur_img = dsc[cur].img;
     }
     if (TMA && tid == 0 && pa >= 0) {  // the previous subdomain's u and p1 bands
       tma_store_2d(&M->u, smem + L::OU, pc0, pgb);
@@ -441,7 +484,17 @@ __device__ __forceinline__ void fused_mt4_body(const Src& S, const Mt4Maps* M, c
       }
     }
     __syncthreads();  // staging consumed by every thread
-    if (t + stride < T) prefetch(t + stride);
+    int nxt = cur;  // slot of the next subdomain's descriptor
+    if constexpr (Src::kBatch) {
+      if (t + stride < T && img_next != dsc[cur].img) {
+        nxt = cur ^ 1;
+        load_batch_desc(&dsc[nxt], S.B, img_next, tid, NT);
+        __syncthreads();
+      }
+      if (t + stride < T) prefetch(t + stride, dsc[nxt].A, t + stride - dsc[nxt].base);
+    } else {
+      if (t + stride < T) prefetch(t + stride, S.args(t + stride), S.local(t + stride));
+    }
 
     // unrolled by two: the new dual values then land in the registers the old ones of
     // the previous iteration held, instead of being moved back every iteration
@@ -676,7 +729,17 @@ __device__ __forceinline__ void fused_mt4_body(const Src& S, const Mt4Maps* M, c
       pc0 = c0;
       pgb = gb;
     }
-    });  // dispatch
+    cur = nxt;
+    };  // body
+    if constexpr (Src::kBatch) {
+      switch (dsc[cur].fid) {
+        case FID_L2: body(FidC<FID_L2>{}); break;
+        case FID_L1: body(FidC<FID_L1>{}); break;
+        default: body(FidC<FID_SEG>{}); break;
+      }
+    } else {
+      S.dispatch(t, body);
+    }
   }
   if (TMA && pa >= 0) {  // the last subdomain's bands
     __syncthreads();
@@ -756,12 +819,18 @@ int& mt4_batch_clusters(int dev) {
   return n[dev & 63];
 }
 
+// the batch kernel keeps its descriptors in the P1 out-buffer region: it is launched with
+// the tensor-copy kernel's shared-memory size
+static_assert(2 * sizeof(Mt4BatchDesc) <= sizeof(float) * Mt4Layout::BAND * Mt4Layout::BW &&
+                  Mt4Layout::OP1 >= Mt4Layout::MB + 6,
+              "two descriptors fit the P1 out-buffer, clear of the cp.async kernel's mbarriers");
+
 cudaError_t prepare_mt4_batch() {
   cudaError_t e = cudaFuncSetAttribute(k_fused_mt4_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)Mt4Layout::BYTES);
+                                       (int)Mt4Layout::BYTES_TMA);
   if (e != cudaSuccess) return e;
   cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t cfg = mt4_config(1024, false, attr);
+  cudaLaunchConfig_t cfg = mt4_config(1024, true, attr);
   int n = 0;
   if (cudaOccupancyMaxActiveClusters(&n, k_fused_mt4_batch, &cfg) != cudaSuccess) {
     cudaGetLastError();
@@ -875,7 +944,7 @@ cudaError_t launch_fused_mt4_batch(const BatchArgs& B, int total_tiles, cudaStre
   cudaGetDevice(&dev);
   const int nc = mt4_batch_clusters(dev);
   cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t cfg = mt4_config((nc <= 0 || nc > total_tiles) ? total_tiles : nc, false, attr);
+  cudaLaunchConfig_t cfg = mt4_config((nc <= 0 || nc > total_tiles) ? total_tiles : nc, true, attr);  // smem size
   cfg.stream = st;
   return cudaLaunchKernelEx(&cfg, k_fused_mt4_batch, B, total_tiles);
 }
