@@ -698,7 +698,9 @@ def run_ours(args):
                  "ms_per_outer": ms_b,
                  "value": bt.pixels() * INNER / (ms_b * 1e-3) / 1e6, "unit": UNIT,
                  "launch": f"one CUDA graph of {n_b} outer iterations (2 kernels per outer iteration: batched "
-                           "multiplier update, persistent clusters over the (image, subdomain) work list)"}
+                           "multiplier update, persistent clusters over the (image, subdomain) work list)",
+                 "kernel": "k_fused_mt4_batch: the 4x4 micro-tile kernel over the work list (cp.async copies, "
+                           "per-image descriptors cached in shared memory)"}
         smem_peak_b = L.measure_smem_bandwidth()
         ach_b = SMEM_BYTES_PER_PX_ITER * bt.pixels() * INNER / (ms_b * 1e-3) / 1e9
         batch["roofline"] = {"bound": "smem", "achieved": ach_b, "peak": smem_peak_b, "unit": "GB/s",
