@@ -569,7 +569,13 @@ __device__ __forceinline__ void fused_mt4_body(const Src& S, const Mt4Maps* M, c
               un = fma2(UB, fg, mul2(UA, ub));
               if (MASK) un = pk2(dl ? lo2(ub) : lo2(un), dh ? hi2(ub) : hi2(un));
             } else {
-              un = pk2(prox_ubar<FID>(lo2(ub), lo2(fg), dl, co), prox_ubar<FID>(hi2(ub), hi2(fg), dh, co));
+              if (FID == FID_L1) {  // ubar - P_[-s,s](ubar - f), packed (the scalar prox_ubar's arithmetic)
+                const f32x2 v = sub2(ub, fg);
+                un = sub2(ub, pk2(clamp_abs(lo2(v), co.s), clamp_abs(hi2(v), co.s)));
+                if (MASK) un = pk2(dl ? lo2(ub) : lo2(un), dh ? hi2(ub) : hi2(un));
+              } else {
+                un = pk2(prox_ubar<FID>(lo2(ub), lo2(fg), dl, co), prox_ubar<FID>(hi2(ub), hi2(fg), dh, co));
+              }
             }
             U[c][e] = un;
           }

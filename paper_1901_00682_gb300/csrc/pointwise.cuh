@@ -41,6 +41,16 @@ __device__ __forceinline__ float u_update(float u, float d, float fg, bool in_d,
   return prox_ubar<FID>(fmaf(c.sig, d, u), fg, in_d, c);
 }
 
+// Projection onto [-lim, lim] (lim >= 0), the pointwise constraint set of the dual
+// field (|p| <= 1 on an edge, 0 on an edge of the image boundary): one min.xorsign.abs,
+// whose magnitude is min(|x|, lim) and whose sign is sign(x) xor sign(lim) = sign(x);
+// the value of fminf(fmaxf(x, -lim), lim) for every x that is not NaN.
+__device__ __forceinline__ float clamp_abs(float x, float lim) {
+  float r;
+  asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(x), "f"(lim));
+  return r;
+}
+
 // prox_{sigma_k alpha F} at ubar = u + sigma_k div pbar
 template <int FID>
 __device__ __forceinline__ float prox_ubar(float ubar, float fg, bool in_d, const Coef& c) {
@@ -50,25 +60,15 @@ __device__ __forceinline__ float prox_ubar(float ubar, float fg, bool in_d, cons
   }
   if (in_d) return ubar;
   if (FID == FID_L2) return fmaf(c.ub, fg, c.ua * ubar);
-  // L1: f + shr(ubar - f, s), shr(v, s) = max(|v| - s, 0) sign(v)
+  // L1: f + shr(ubar - f, s) with shr(v, s) = max(|v| - s, 0) sign(v), evaluated as
+  // ubar - P_[-s,s](ubar - f) (the same map: v - P(v) = shr(v, s)), one projection
   const float v = ubar - fg;
-  const float m = fabsf(v) - c.s;
-  return m > 0.0f ? fg + copysignf(m, v) : fg;
+  return ubar - clamp_abs(v, c.s);
 }
 
 // Argument of the projection in the p-step: (tau (p + tau_k Du) + tau_k phat) / (tau + tau_k).
 __device__ __forceinline__ float p_target(float p, float du, float phat, const Coef& c) {
   return fmaf(c.pc, du, fmaf(c.pa, p, c.pb * phat));
-}
-
-// Projection onto [-lim, lim] (lim >= 0), the pointwise constraint set of the dual
-// field (|p| <= 1 on an edge, 0 on an edge of the image boundary): one min.xorsign.abs,
-// whose magnitude is min(|x|, lim) and whose sign is sign(x) xor sign(lim) = sign(x);
-// the value of fminf(fmaxf(x, -lim), lim) for every x that is not NaN.
-__device__ __forceinline__ float clamp_abs(float x, float lim) {
-  float r;
-  asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(x), "f"(lim));
-  return r;
 }
 
 // One dof of the p-step: q = p + tau_k Du, p_new = proj_[-1,1]((tau q + tau_k phat) /
