@@ -30,6 +30,10 @@
 // is rewritten only after a wait for the copies to have read it); p2 and the sides go
 // out with ordinary stores.
 //
+// Batch: k_fused_mt4_batch runs the cp.async form of the body over the work list of a
+// batch of images (BatchTiles), every subdomain with its image's descriptor (kept in
+// shared memory while the image does not change), fidelity and coefficients.
+//
 // ADAPT (tensor-copy kernel only): adaptive inner stopping (Section 5, eq. stop_inner1).
 // Every thread sums (p^{k+1} - p^k)^2 and (p^{k+1})^2 over its dofs in the p-step of
 // iteration k (packed float32 pairs) and leaves them in the P1 out-buffer, idle during
