@@ -27,3 +27,20 @@ def test_salt_pepper_and_mask_rates():
     changed = f[keep] != clean[keep]
     assert abs(changed.mean() - 0.1 * (1 - np.mean((clean[keep] == 0) | (clean[keep] == 1)))) < 0.02
     assert set(np.unique(f[keep][changed])) <= {0.0, 1.0}
+
+
+def test_batch_workload_shapes():
+    """Config 4: 64 images with short side s in {256, 512, 1024, 2048} and aspect 1:1,
+    2:1 or 1:2 (s x s, s x 2s, 2s x s), even ROF and odd segmentation; every side a
+    multiple of 128 (the batch's subdomain side); the draw of seed 0 is deterministic."""
+    ims = synth.batch_workload(64, 0)
+    assert len(ims) == 64
+    for i, m in enumerate(ims):
+        h, w = m["height"], m["width"]
+        s, l = min(h, w), max(h, w)
+        assert s in (256, 512, 1024, 2048) and l in (s, 2 * s)
+        assert h % 128 == 0 and w % 128 == 0 and m["f"].shape == (h, w)
+        assert m["fidelity"] == ("l2" if i % 2 == 0 else "seg")
+    assert sum(m["height"] * m["width"] for m in ims) == 168230912
+    a, b = synth.batch_workload(3, 0), synth.batch_workload(3, 0)
+    assert all(np.array_equal(x["f"], y["f"]) for x, y in zip(a, b))
