@@ -29,23 +29,24 @@ def _images():
     return out
 
 
-@pytest.mark.parametrize("tile,variant", [(128, 0), (128, 2), (64, 0)])
-def test_batch_equals_single_image_solves_bitwise(tile, variant):
+@pytest.mark.parametrize("tile,variant,K", [(128, 0, 10), (128, 2, 10), (64, 0, 10), (128, 0, 70)])
+def test_batch_equals_single_image_solves_bitwise(tile, variant, K):
     """The batch kernels (128: persistent clusters over the work list, 4 x 4 micro-tiles
     (variant 0) or 2 x 4 (variant 2); 64: one CTA per subdomain) give each image the
     bits of its own solve.  Every image here has W + N_c not a multiple of 4, so the
     4 x 4 kernel copies their p2 rows 4 bytes at a time (the full-workload test below
-    covers the 16-byte copies)."""
+    covers the 16-byte copies).  K = 70 exceeds the 4 x 4 kernel's coefficient table:
+    variant 0 then runs the 2 x 4 kernel, as the single-image path does."""
     L = _lib()
     ims = _images()
-    b = L.Batch(ims, inner_iters=10, tile=tile, variant=variant)
+    b = L.Batch(ims, inner_iters=K, tile=tile, variant=variant)
     fs = [torch.from_numpy(m["f"]).cuda() for m in ims]
     b.load(fs)
     b.iterate(13)
     for k, m in enumerate(ims):
         u_b = b.get_u(k, torch.empty_like(fs[k]))
         p = L.make_params(m["height"], m["width"], m["height"] // tile, m["width"] // tile, fidelity=m["fidelity"],
-                          alpha=m["alpha"], c1=m["c1"], c2=m["c2"], inner_iters=10)
+                          alpha=m["alpha"], c1=m["c1"], c2=m["c2"], inner_iters=K)
         s = L.Solver(p)
         s.load(fs[k])
         s.iterate(13)
